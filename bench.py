@@ -1,0 +1,421 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the fused D2Q9 SmrtLBM step on GB300.
+
+One "step" is one application of the update (pull-stream + bounce-back +
+moments + f^eq + SmrtLBM collision + store) over the whole lattice.  The
+default workload is the periodic Taylor-Green vortex on 8192 x 8192 nodes
+(u0 = 0.05, k = 2 pi / 8192, tau = 0.51), FP32 storage of f - w, two-buffer
+layout; inputs (4.8 GB of populations) exceed the 129 MB L2, so no flush is
+needed between steps.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+(a deliberately slow, plain program) on a bounded window of the same workload.
+Multi-GPU runs are independent replicas (the update needs no collective).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+BYTES_PER_NODE = {"f64": 144, "f32": 72, "f16": 36, "bf16": 36}
+ORACLE_RATE_GUESS = 2.5e6     # node updates / s of the FP64 oracle on one core, for sizing samples
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=["tgv8192", "cavity4096"], default="tgv8192")
+    p.add_argument("--layout", choices=["ab", "aa"], default="ab")
+    p.add_argument("--prec", choices=["f32", "f16", "bf16", "f64"], default="f32")
+    p.add_argument("--kind", choices=["smrt", "srt"], default="smrt")
+    p.add_argument("--variant-steps", type=int, default=2000,
+                   help="steps per extra variant line (0 disables the variants)")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args(argv)
+
+
+def workload(name):
+    from paper_2409_01076_gb300 import workloads as W
+    if name == "tgv8192":
+        return dict(name="tgv8192", nx=8192, ny=8192, tau=0.51, u_lid=0.0, bc=W.ALL_PERIODIC, u0=0.05,
+                    desc="periodic Taylor-Green vortex 8192x8192, u0=0.05, k=2pi/8192, tau=0.51")
+    n, U, re = 4096, 0.1, 1e4
+    return dict(name="cavity4096", nx=n, ny=n, tau=W.cavity_tau(n, U, re), u_lid=U, bc=W.CAVITY, u0=None,
+                desc="lid-driven cavity 4096x4096, Re=10000, U_lid=0.1, halfway bounce-back")
+
+
+def initial_fields(wl):
+    """Seeded/analytic initial (rho, u) on the host, float64."""
+    from paper_2409_01076_gb300 import workloads as W
+    if wl["u0"] is not None:
+        return W.tgv_fields(wl["nx"], wl["ny"], wl["u0"])
+    return W.rest_fields(wl["nx"], wl["ny"])
+
+
+# ---- distributed plumbing (replicas only) ----------------------------------------
+
+def dist_setup(n_gpus):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    """Largest value of x over all ranks (the job is as slow as its slowest rank)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---- clocks during the timed region ------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, local_rank):
+        self.proc = None
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [v for v in vis.split(",") if v.strip()]
+        self.index = ids[local_rank] if local_rank < len(ids) and ids[local_rank].strip().isdigit() else str(local_rank)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.index, "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, power, reasons = [], [], [], set()
+        for line in out.splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, val in zip(self.NAMES, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        load = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ---- measured peaks and committed ncu traffic ------------------------------------------
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2409_01076_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as fh:
+                h.update(name.encode() + b"\0" + fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(prec, layout, kind):
+    """DRAM bytes per node update of the step kernel from the committed ncu summary, if it
+    was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None, None
+    key = "%s-%s-%s" % (prec, layout, kind)
+    src = None
+    val = None
+    for line in text.splitlines():
+        if line.startswith("source_hash:"):
+            src = line.split(":", 1)[1].strip()
+        if line.startswith("traffic_bytes_per_node[%s]:" % key):
+            val = float(line.split(":", 1)[1].strip())
+    if val is None or src != kernel_source_hash():
+        return None, src
+    return val, src
+
+
+# ---- the GPU arm ---------------------------------------------------------------------
+
+def make_handle(S, wl, prec, layout, kind, check=True):
+    h = S.smrt_create(wl["nx"], wl["ny"], wl["tau"], wl["u_lid"], wl["bc"])
+    S.smrt_set_option(h, S.SMRT_OPT_PRECISION, {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}[prec])
+    S.smrt_set_option(h, S.SMRT_OPT_LAYOUT, {"ab": 0, "aa": 1}[layout])
+    S.smrt_set_option(h, S.SMRT_OPT_COLLISION, {"smrt": 0, "srt": 1}[kind])
+    S.smrt_set_option(h, S.SMRT_OPT_CHECK_DIVERGENCE, 1 if check else 0)
+    return h
+
+
+def time_steps(S, h, steps, world):
+    """CUDA-event time (ms) of `steps` updates on the handle's stream (the legacy default stream)."""
+    import torch
+    barrier(world)
+    torch.cuda.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record()
+    S.smrt_step(h, steps)
+    end.record()
+    torch.cuda.synchronize()
+    barrier(world)
+    return start.elapsed_time(end)
+
+
+def run_variant(S, wl, rho_d, u_d, prec, layout, kind, steps, warmup, world):
+    h = make_handle(S, wl, prec, layout, kind)
+    if wl["u0"] is not None:
+        S.smrt_init_macros(h, rho_d, u_d)
+    S.smrt_step(h, warmup)
+    ms = max_over_ranks(time_steps(S, h, steps, world), world)
+    S.smrt_destroy(h)
+    nodes = wl["nx"] * wl["ny"]
+    mlups = nodes * steps / (ms * 1e-3) / 1e6
+    return {"mlups": round(mlups, 1), "ms_per_step": round(ms / steps, 5),
+            "hbm_gbs": round(BYTES_PER_NODE[prec] * nodes / (ms / steps * 1e-3) / 1e9, 1), "steps": steps}
+
+
+def e2e_run(S, wl, prec, layout, kind, steps, world):
+    """Same metric through the public C ABI with host buffers: pinned host (rho, u)
+    in, K updates, pinned host (rho, u) out, all inside the timed region."""
+    import torch
+    rho, u = initial_fields(wl)
+    rho_h = torch.from_numpy(rho).pin_memory()
+    u_h = torch.from_numpy(u).pin_memory()
+    rho_o = torch.empty_like(rho_h).pin_memory()
+    u_o = torch.empty_like(u_h).pin_memory()
+    h = make_handle(S, wl, prec, layout, kind)
+    S.smrt_step(h, 1)                      # allocate the state outside the timed region
+    S.smrt_macros(h, rho_o, u_o)           # and the staging buffer
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    S.smrt_init_macros(h, rho_h, u_h)
+    S.smrt_step(h, steps)
+    S.smrt_macros(h, rho_o, u_o)
+    t1 = time.perf_counter()
+    barrier(world)
+    S.smrt_destroy(h)
+    sec = max_over_ranks(t1 - t0, world)
+    nodes = wl["nx"] * wl["ny"]
+    h2d = rho_h.numel() * 8 + u_h.numel() * 8
+    d2h = rho_o.numel() * 8 + u_o.numel() * 8
+    finite = bool(torch.isfinite(u_o).all())
+    return {"value": round(world * nodes * steps / sec / 1e6, 1), "unit": "MLUPS",
+            "h2d_bytes_per_step": round(h2d / steps, 1), "d2h_bytes_per_step": round(d2h / steps, 1),
+            "h2d_bytes_total": h2d, "d2h_bytes_total": d2h, "seconds": round(sec, 4), "steps": steps,
+            "api": "smrt_init_macros(host) + smrt_step(K) + smrt_macros(host)", "result_finite": finite}
+
+
+# ---- the CPU oracle (baseline / reference arm) ------------------------------------------------
+
+def oracle_sample(wl, side, steps):
+    """Time the FP64 oracle on a side x side window of the same workload; returns (MLUPS, seconds)."""
+    import oracle as O
+    from paper_2409_01076_gb300 import workloads as W
+    if wl["u0"] is not None:
+        rho, u = W.tgv_fields(wl["nx"], wl["ny"], wl["u0"], 0, 0, side, side)
+        f0 = O.init_equilibrium(rho, u)
+        bc = O.ALL_PERIODIC
+    else:
+        f0 = O.cavity_initial(side, side)
+        bc = O.CAVITY
+    t0 = time.perf_counter()
+    O.run(f0, steps, bc, wl["tau"], u_lid=wl["u_lid"])
+    sec = time.perf_counter() - t0
+    return side * side * steps / sec / 1e6, sec
+
+
+def cpu_baseline(wl, budget_s=12.0):
+    side = 512
+    steps = max(1, int(budget_s * ORACLE_RATE_GUESS / (side * side)))
+    mlups, sec = oracle_sample(wl, side, steps)
+    return {"value": round(mlups, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": "%dx%d window of the same workload (%s), %d steps, single-threaded FP64 C oracle, %.1f s"
+                      % (side, side, wl["name"], steps, sec)}
+
+
+def reference_arm(args):
+    rank, world, _ = dist_setup(args.gpus)
+    if rank != 0:
+        return 0
+    wl = workload(args.workload)
+    total = args.steps + args.warmup
+    side = int(math.sqrt(60.0 * ORACLE_RATE_GUESS / max(total, 1)))
+    side = max(16, min(1024, side))
+    for _ in range(args.warmup):
+        oracle_sample(wl, side, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_sample(wl, side, 1)
+    sec = time.perf_counter() - t0
+    mlups = side * side * args.steps / sec / 1e6
+    line = {
+        "impl": "reference", "metric": "D2Q9 SmrtLBM MLUPS", "value": round(mlups, 4), "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(sec / args.steps * 1e3, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["desc"], "sample": "%dx%d window per step" % (side, side),
+                   "l2": "CPU run; no GPU L2 involved"},
+        "cpu_baseline": {"value": round(mlups, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": "%dx%d window of %s, one update per step, single-threaded FP64 C oracle"
+                                   % (side, side, wl["name"])},
+        "e2e": {"value": round(mlups, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def gpu_arm(args):
+    import torch
+    import paper_2409_01076_gb300 as S
+
+    rank, world, local = dist_setup(args.gpus)
+    wl = workload(args.workload)
+    nodes = wl["nx"] * wl["ny"]
+    S._lib.load()
+
+    rho, u = initial_fields(wl)
+    rho_d = torch.from_numpy(rho).cuda()
+    u_d = torch.from_numpy(u).cuda()
+    del rho, u
+
+    h = make_handle(S, wl, args.prec, args.layout, args.kind)
+    S.smrt_init_macros(h, rho_d, u_d)
+    S.smrt_step(h, max(args.warmup, 3))
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms = time_steps(S, h, args.steps, world)
+    clk = clocks.stop()
+    r, sums = S.smrt_residual(h)
+    S.smrt_destroy(h)
+    ms = max_over_ranks(ms, world)
+    sec = ms * 1e-3
+    mlups = world * nodes * args.steps / sec / 1e6
+    per_launch = sec / args.steps
+    peak, peak_src = measured_hbm_peak()
+    achieved = BYTES_PER_NODE[args.prec] * nodes / per_launch / 1e9
+    traffic_per_node, _ = committed_traffic(args.prec, args.layout, args.kind)
+
+    result = {
+        "metric": "D2Q9 SmrtLBM MLUPS + % HBM roofline", "value": round(mlups, 1), "unit": "MLUPS",
+        "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
+        "ms_per_step": round(ms / args.steps, 5), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.prec == "f32" else args.prec, "data": "synthetic",
+        "config": {"workload": wl["desc"], "nodes": nodes, "storage": "%s offsets f - w" % args.prec,
+                   "layout": args.layout, "collision": args.kind,
+                   "l2": "no flush: populations (%.2f GB) exceed the 129 MB L2"
+                         % (BYTES_PER_NODE[args.prec] / 2 * nodes * (2 if args.layout == "ab" else 1) / 1e9),
+                   "parallelism": "replicas x%d" % world},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src
+                     if peak_src == "measured" else "fallback 6.8 TB/s",
+                     "traffic": (round(traffic_per_node * nodes) if traffic_per_node else None),
+                     "algorithmic_bytes_per_launch": BYTES_PER_NODE[args.prec] * nodes,
+                     "kernel": "step_kernel<%s,%s,%s>" % (args.prec, args.kind, args.layout)},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+        "check": {"residual_after": r, "mass_rel_err": abs(sums[0] / nodes - 1.0)},
+    }
+
+    if args.variant_steps > 0:
+        variants = {}
+        vs = args.variant_steps
+        for prec, layout, kind in [("f32", "ab", "srt"), ("f32", "aa", "smrt"), ("f32", "aa", "srt"),
+                                   ("f16", "ab", "smrt"), ("bf16", "ab", "smrt"), ("f16", "aa", "smrt")]:
+            if (prec, layout, kind) == (args.prec, args.layout, args.kind):
+                continue
+            variants["%s-%s-%s" % (prec, layout, kind)] = run_variant(S, wl, rho_d, u_d, prec, layout, kind, vs,
+                                                                      10, world)
+        if wl["name"] == "tgv8192":
+            cav = workload("cavity4096")
+            for layout, kind in [("ab", "smrt"), ("ab", "srt"), ("aa", "smrt")]:
+                variants["cavity4096-f32-%s-%s" % (layout, kind)] = run_variant(
+                    S, cav, None, None, "f32", layout, kind, vs, 10, world)
+        result["variants"] = variants
+
+    del rho_d, u_d
+    torch.cuda.empty_cache()
+    if not args.no_e2e:
+        result["e2e"] = e2e_run(S, wl, args.prec, args.layout, args.kind, args.steps, world)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        result["cpu_baseline"] = cpu_baseline(wl)
+    elif not args.no_cpu:
+        result["cpu_baseline"] = None
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return reference_arm(args)
+    return gpu_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,192 @@
+/*
+ * smrt.h -- C ABI of libsmrt, a GB300 (sm_103a) implementation of the D2Q9
+ * Single MRT-featured Lattice Boltzmann Method (SmrtLBM) of
+ * J. G. Zhou, arXiv 2409.01076.
+ *
+ * The library advances a 2-D lattice of nx x ny nodes with the fused
+ * stream-and-collide update of Eq. (SmrtLBM-1):
+ *
+ *   f_a(x + e_a, t + 1) = f_a^eq(x, t)
+ *       + (-1)^a (1 - 1/tau) sum_{k=1}^{8} (-1)^k / 4
+ *             [1_{1234}(a, k) + 1_{5678}(a, k)] (f_k(x, t) - f_k^eq(x, t)),
+ *
+ * with f^eq of Eq. (feq-full), rho and u of Eq. (fea-0), the indicator of
+ * Eq. (indicator-fn), and the D2Q9 velocities e_a in the paper's order
+ * (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),(-1,-1),(1,-1).  The SRT-LBM
+ * update of Eq. (lb.srt) and the two-relaxation-time form of
+ * Eq. (SmrtLBM-lb.1.5) are selectable collision kinds of the same kernels.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every call returns an smrt_status; on failure smrt_last_error() explains.
+ *   Nothing is freed that the caller owns; the library owns only what
+ *   smrt_create/smrt_destroy manage.
+ * - Node (i, j): i = 0..nx-1 along x, j = 0..ny-1 along y, the top side at
+ *   j = ny-1.  Field arrays are row-major, index j*nx + i, with no padding.
+ *     f   : double[9][ny][nx]       (population a, row j, column i)
+ *     rho : double[ny][nx]
+ *     u   : double[2][ny][nx]       (the u_x plane, then the u_y plane)
+ * - Pointers may be host memory (pageable or pinned) or device memory of the
+ *   current CUDA device; the library tells them apart with
+ *   cudaPointerGetAttributes.  Device-pointer calls run on the handle's
+ *   stream; host-pointer calls return after the copy completed.
+ * - The canonical state f(t) is the post-streaming, pre-collision field, i.e.
+ *   the left-hand side of Eq. (SmrtLBM-1) after t updates; rho(t), u(t) are its
+ *   moments (Eq. fea-0).  t counts applications of the update.
+ * - Boundaries (the paper's cavity: "standard bounce-back" on three walls, a
+ *   lid moving with u_x = u0, u_y = 0): halfway (link) bounce-back; a moving
+ *   wall adds -6 w_a rho_w (e_a . u_w) to the returning population, with
+ *   rho_w = 1.  A link that leaves through a bottom/top wall and a left/right
+ *   side at once takes the bottom/top wall's velocity; a link that leaves
+ *   through a wall in one axis bounces back even if the other axis is
+ *   periodic.
+ * - Not thread-safe per handle: one host thread at a time per smrt_t.
+ */
+#ifndef SMRT_H
+#define SMRT_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define SMRT_API __attribute__((visibility("default")))
+#else
+#define SMRT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct smrt_t smrt_t; /* opaque; owns device buffers, stream binding, flags */
+
+enum smrt_status {
+    SMRT_OK = 0,
+    SMRT_ERR_ARG = -1,      /* invalid argument; nothing was changed          */
+    SMRT_ERR_OOM = -2,      /* device allocation failed or exceeds MEM_LIMIT  */
+    SMRT_ERR_CUDA = -3,     /* a CUDA runtime call failed (message has it)    */
+    SMRT_ERR_DIVERGED = -4, /* some node had rho <= 0 or a non-finite rho     */
+    SMRT_ERR_TIMEOUT = -5,  /* a bounded device-side wait gave up             */
+    SMRT_ERR_STATE = -6     /* call not valid in the handle's current state   */
+};
+
+/* Boundary kind of one side; bc_flags packs 2 bits per side:
+ * left (bits 0-1), right (2-3), bottom (4-5), top (6-7).
+ * A moving wall slides with speed u_lid along its tangent: +x for the bottom
+ * and top sides, +y for the left and right sides.  Periodic sides come in
+ * pairs (left with right, bottom with top). */
+enum smrt_bc { SMRT_BC_PERIODIC = 0, SMRT_BC_WALL = 1, SMRT_BC_MOVING = 2 };
+#define SMRT_BC_FLAGS(left, right, bottom, top) \
+    ((unsigned)(left) | ((unsigned)(right) << 2) | ((unsigned)(bottom) << 4) | ((unsigned)(top) << 6))
+/* lid-driven cavity: resting walls left, right, bottom; moving lid on top */
+#define SMRT_BC_CAVITY SMRT_BC_FLAGS(SMRT_BC_WALL, SMRT_BC_WALL, SMRT_BC_WALL, SMRT_BC_MOVING)
+
+/* smrt_set_option keys and values. */
+enum smrt_option {
+    SMRT_OPT_COLLISION = 1,   /* SMRT_COLLISION_*; any time                               */
+    SMRT_OPT_TAU_S = 2,       /* tau_s of the two-relaxation-time form (> 0.5); any time  */
+    SMRT_OPT_LAYOUT = 3,      /* SMRT_LAYOUT_*; only before the state is first touched    */
+    SMRT_OPT_PRECISION = 4,   /* SMRT_PREC_*;   only before the state is first touched    */
+    SMRT_OPT_CHECK_DIVERGENCE = 5, /* 1 (default): smrt_step syncs and reports DIVERGED;
+                                      0: smrt_step only enqueues                           */
+    SMRT_OPT_MEM_LIMIT = 6,   /* bytes the handle may allocate on the device; 0 = no limit;
+                                 only before the state is first touched                  */
+    SMRT_OPT_TAU = 7          /* change tau (> 0.5); any time                              */
+};
+enum smrt_collision {
+    SMRT_COLLISION_SMRT = 0,    /* Eq. (SmrtLBM-1)                                   */
+    SMRT_COLLISION_SRT = 1,     /* Eq. (lb.srt)                                      */
+    SMRT_COLLISION_TWO_TAU = 2  /* Eq. (SmrtLBM-lb.1.5) with tau_s from SMRT_OPT_TAU_S */
+};
+enum smrt_layout {
+    SMRT_LAYOUT_AB = 0, /* two buffers: pull-stream from A, collide, store to B, swap     */
+    SMRT_LAYOUT_AA = 1  /* one buffer, in place: alternating local / neighbour-swap steps */
+};
+enum smrt_precision {
+    SMRT_PREC_F64 = 0,  /* stored f - w_a in double, double arithmetic         */
+    SMRT_PREC_F32 = 1,  /* stored f - w_a in float, float arithmetic           */
+    SMRT_PREC_F16 = 2,  /* stored f - w_a in IEEE half, float arithmetic       */
+    SMRT_PREC_BF16 = 3  /* stored f - w_a in bfloat16, float arithmetic        */
+};
+
+/* Create a handle for an nx x ny lattice with relaxation time tau (Eq. SmrtLBM-1;
+ * the kinematic viscosity is nu = (2 tau - 1) e dx / 6, Eq. relation-chapman-viscosity),
+ * moving-wall speed u_lid (lattice units) and boundary kinds bc_flags.
+ * Requires nx, ny >= 2, tau > 0.5 (finite), |u_lid| < 1/sqrt(3), valid paired
+ * bc_flags, and 9 * pitch * ny elements addressable.  No CUDA call is made
+ * here: device memory is allocated on the first call that touches the state,
+ * which initialises f(0) = f^eq(rho = 1, u = 0) and t = 0.
+ * On success *out receives the handle; on failure *out is set to NULL and
+ * smrt_last_error(NULL) explains.  Defaults: SMRT collision, AB layout, F64,
+ * divergence check on, legacy default stream. */
+SMRT_API int smrt_create(int nx, int ny, double tau, double u_lid, unsigned bc_flags, smrt_t **out);
+
+/* Set one option (see enum smrt_option).  Options marked "before the state is
+ * first touched" return SMRT_ERR_STATE afterwards. */
+SMRT_API int smrt_set_option(smrt_t *h, int key, double value);
+
+/* Read one option's current value. */
+SMRT_API int smrt_get_option(const smrt_t *h, int key, double *value);
+
+/* Bind the CUDA stream (a cudaStream_t, passed as void*) that every later
+ * launch and copy of this handle uses; NULL selects the legacy default stream.
+ * The caller keeps ownership of the stream and must keep it alive. */
+SMRT_API int smrt_set_stream(smrt_t *h, void *stream);
+
+/* Apply the update n >= 0 times (t += n).  Launches are enqueued on the
+ * handle's stream.  With the divergence check on, the call then waits for the
+ * stream and returns SMRT_ERR_DIVERGED if any node had rho <= 0 or a
+ * non-finite rho during these or earlier unchecked steps (t still advanced);
+ * the flag clears on smrt_set_f / smrt_init_macros. */
+SMRT_API int smrt_step(smrt_t *h, long long n);
+
+/* Wait for the handle's stream; returns SMRT_ERR_DIVERGED if the divergence
+ * flag is set (see smrt_step), else SMRT_OK or SMRT_ERR_CUDA. */
+SMRT_API int smrt_sync(smrt_t *h);
+
+/* Moments rho(t) and u(t) of the canonical state (Eq. fea-0), accumulated in
+ * double.  rho: double[ny][nx]; u: double[2][ny][nx]; either may be NULL. */
+SMRT_API int smrt_macros(smrt_t *h, double *rho, double *u);
+
+/* Steady-state residual without advancing t:
+ *   r = ||u(t+1) - u(t)||_2 / ||u(t+1)||_2 over all nodes (0 when both vanish),
+ * where u(t+1) is what the next update would produce.  The paper states no
+ * criterion; this is the definition used for "steady".  r (host, may be NULL)
+ * receives r; sums (host, may be NULL) receives double[3] =
+ * {sum rho(t), sum rho u_x(t), sum rho u_y(t)}.  All accumulation is double. */
+SMRT_API int smrt_residual(smrt_t *h, double *r, double *sums);
+
+/* Copy the canonical state f(t) out as double[9][ny][nx]. */
+SMRT_API int smrt_get_f(smrt_t *h, double *f);
+
+/* Replace the canonical state by f (double[9][ny][nx]); t is unchanged and the
+ * divergence flag clears.  Values are rounded to the storage precision. */
+SMRT_API int smrt_set_f(smrt_t *h, const double *f);
+
+/* Replace the state by f = f^eq(rho, u) of Eq. (feq-full) at every node
+ * (rho: double[ny][nx], u: double[2][ny][nx]); t is unchanged, the divergence
+ * flag clears. */
+SMRT_API int smrt_init_macros(smrt_t *h, const double *rho, const double *u);
+
+/* Number of updates applied so far (t); -1 for a NULL handle. */
+SMRT_API long long smrt_time(const smrt_t *h);
+
+/* Set t (>= 0) without touching the populations.  With the AA layout the
+ * stored arrangement depends on the parity of t, so this is allowed only
+ * while the parity stays the same (else SMRT_ERR_STATE). */
+SMRT_API int smrt_set_time(smrt_t *h, long long t);
+
+/* Bytes of device memory the handle holds (0 before the state is touched). */
+SMRT_API size_t smrt_device_bytes(const smrt_t *h);
+
+/* Last error message of h, or of the calling thread's last failed
+ * smrt_create when h is NULL.  Never NULL; valid until the next call on h. */
+SMRT_API const char *smrt_last_error(const smrt_t *h);
+
+/* Free the handle's device memory and the handle.  NULL is ignored. */
+SMRT_API void smrt_destroy(smrt_t *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SMRT_H */

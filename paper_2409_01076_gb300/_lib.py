@@ -1,0 +1,57 @@
+"""ctypes loader for libsmrt.so (the C ABI of include/smrt.h).
+
+The library is built in-tree by build_lib.py.  There is no fallback: if the
+shared library cannot be built or loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+from . import build_lib
+
+_lock = threading.Lock()
+_lib: ctypes.CDLL | None = None
+
+c_int, c_uint, c_double, c_longlong, c_size_t, c_void_p, c_char_p = (
+    ctypes.c_int, ctypes.c_uint, ctypes.c_double, ctypes.c_longlong, ctypes.c_size_t,
+    ctypes.c_void_p, ctypes.c_char_p)
+
+# (name, restype, argtypes) for every function declared in include/smrt.h
+SIGNATURES = [
+    ("smrt_create", c_int, [c_int, c_int, c_double, c_double, c_uint, ctypes.POINTER(c_void_p)]),
+    ("smrt_set_option", c_int, [c_void_p, c_int, c_double]),
+    ("smrt_get_option", c_int, [c_void_p, c_int, ctypes.POINTER(c_double)]),
+    ("smrt_set_stream", c_int, [c_void_p, c_void_p]),
+    ("smrt_step", c_int, [c_void_p, c_longlong]),
+    ("smrt_sync", c_int, [c_void_p]),
+    ("smrt_macros", c_int, [c_void_p, c_void_p, c_void_p]),
+    ("smrt_residual", c_int, [c_void_p, c_void_p, c_void_p]),
+    ("smrt_get_f", c_int, [c_void_p, c_void_p]),
+    ("smrt_set_f", c_int, [c_void_p, c_void_p]),
+    ("smrt_init_macros", c_int, [c_void_p, c_void_p, c_void_p]),
+    ("smrt_time", c_longlong, [c_void_p]),
+    ("smrt_set_time", c_int, [c_void_p, c_longlong]),
+    ("smrt_device_bytes", c_size_t, [c_void_p]),
+    ("smrt_last_error", c_char_p, [c_void_p]),
+    ("smrt_destroy", None, [c_void_p]),
+]
+
+
+def path() -> str:
+    return build_lib.LIB
+
+
+def load() -> ctypes.CDLL:
+    """Build (if stale) and load libsmrt.so; raises if that is impossible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib_path = build_lib.build()
+            L = ctypes.CDLL(lib_path)
+            for name, res, args in SIGNATURES:
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib

@@ -1,0 +1,285 @@
+// d2q9.cuh -- device-side building blocks of the SmrtLBM kernels (sm_103a).
+//
+// Lattice constants, storage formats, kernel parameters, the boundary
+// resolution of a pulled population and the per-node collision operators.
+// Everything here is GPU-side code of this library; it shares nothing with the
+// CPU oracle.
+//
+// Storage: every precision stores the offset g_a = f_a - w_a of each population
+// (w_a the D2Q9 weight), which keeps the stored numbers small (|g| ~ |u| w) and
+// so gains relative precision in every format; rho = 1 + sum g.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace smrt {
+
+// ---- D2Q9 velocity set in the paper's order (listing below Eq. lb.srt) -------
+// a: 0 (0,0), 1 (1,0), 2 (0,1), 3 (-1,0), 4 (0,-1), 5 (1,1), 6 (-1,1), 7 (-1,-1), 8 (1,-1)
+__host__ __device__ constexpr int ex(int a)
+{
+    return (a == 1 || a == 5 || a == 8) ? 1 : ((a == 3 || a == 6 || a == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int ey(int a)
+{
+    return (a == 2 || a == 5 || a == 6) ? 1 : ((a == 4 || a == 7 || a == 8) ? -1 : 0);
+}
+// reversed link: 1<->3, 2<->4, 5<->7, 6<->8
+__host__ __device__ constexpr int opp(int a)
+{
+    return a == 0 ? 0 : (a <= 4 ? ((a + 1) % 4) + 1 : ((a - 3) % 4) + 5);
+}
+// weights below Eq. (feq-full)
+template <class C>
+__host__ __device__ constexpr C wgt(int a)
+{
+    return a == 0 ? C(4) / C(9) : (a <= 4 ? C(1) / C(9) : C(1) / C(36));
+}
+static_assert(opp(1) == 3 && opp(3) == 1 && opp(2) == 4 && opp(4) == 2, "opp");
+static_assert(opp(5) == 7 && opp(7) == 5 && opp(6) == 8 && opp(8) == 6, "opp");
+static_assert(ex(opp(6)) == -ex(6) && ey(opp(6)) == -ey(6), "opp");
+
+// ---- storage formats ----------------------------------------------------------
+// R: the raw stored type; C: the arithmetic type.
+template <int PREC> struct Prec;
+template <> struct Prec<SMRT_PREC_F64> {
+    using R = double;
+    using C = double;
+    static __device__ __forceinline__ C to_c(R r) { return r; }
+    static __device__ __forceinline__ R to_r(C c) { return c; }
+};
+template <> struct Prec<SMRT_PREC_F32> {
+    using R = float;
+    using C = float;
+    static __device__ __forceinline__ C to_c(R r) { return r; }
+    static __device__ __forceinline__ R to_r(C c) { return c; }
+};
+template <> struct Prec<SMRT_PREC_F16> {
+    using R = unsigned short;
+    using C = float;
+    static __device__ __forceinline__ C to_c(R r) { return __half2float(__ushort_as_half(r)); }
+    static __device__ __forceinline__ R to_r(C c) { return __half_as_ushort(__float2half_rn(c)); }
+};
+template <> struct Prec<SMRT_PREC_BF16> {
+    using R = unsigned short;
+    using C = float;
+    static __device__ __forceinline__ C to_c(R r) { return __bfloat162float(__ushort_as_bfloat16(r)); }
+    static __device__ __forceinline__ R to_r(C c) { return __bfloat16_as_ushort(__float2bfloat16_rn(c)); }
+};
+
+// ---- kernel parameters --------------------------------------------------------
+enum { SIDE_LEFT = 0, SIDE_RIGHT = 1, SIDE_BOTTOM = 2, SIDE_TOP = 3 };
+
+template <class C>
+struct Params {
+    int nx, ny;
+    int pitch;          // elements per stored row (>= nx, 128-byte multiple)
+    long long plane;    // elements per population plane (pitch * ny)
+    int periodic_x;     // left/right periodic
+    int periodic_y;     // bottom/top periodic
+    C omega;            // 1 / tau
+    C omega_s;          // 1 / tau_s (two-relaxation-time form)
+    C a4;               // (1 - 1/tau) / 4, SmrtLBM
+    C trt4;             // (1/tau_s - 1/tau) / 4, two-relaxation-time form
+    C corr[4][9];       // moving-wall term 6 w_a (e_a . u_w(side)) added to a wall-pulled offset
+    int *flag;          // divergence flag (bit 0)
+};
+
+template <class C>
+inline Params<C> make_params(const HostParams &h)
+{
+    Params<C> p;
+    p.nx = h.nx;
+    p.ny = h.ny;
+    p.pitch = h.pitch;
+    p.plane = h.plane;
+    p.periodic_x = ((h.bc & 3u) == SMRT_BC_PERIODIC);
+    p.periodic_y = (((h.bc >> 4) & 3u) == SMRT_BC_PERIODIC);
+    p.omega = C(1.0 / h.tau);
+    p.omega_s = C(1.0 / h.tau_s);
+    p.a4 = C((1.0 - 1.0 / h.tau) / 4.0);
+    p.trt4 = C((1.0 / h.tau_s - 1.0 / h.tau) / 4.0);
+    for (int s = 0; s < 4; ++s) {
+        unsigned kind = (h.bc >> (2 * s)) & 3u;
+        double wx = 0.0, wy = 0.0;
+        if (kind == SMRT_BC_MOVING) {
+            if (s == SIDE_BOTTOM || s == SIDE_TOP) wx = h.u_lid;
+            else wy = h.u_lid;
+        }
+        for (int a = 0; a < 9; ++a)
+            p.corr[s][a] = C(6.0 * wgt<double>(a) * (ex(a) * wx + ey(a) * wy));
+    }
+    p.flag = h.flag;
+    return p;
+}
+
+// ---- boundary resolution --------------------------------------------------------
+// Where a canonical population f_a(i, j) is found in storage.  `side` >= 0 marks a
+// wall link (the pull source lies behind a wall on that side) whose stored value
+// needs the moving-wall term p.corr[side][a] added.
+struct Loc {
+    int plane, j, i, side;
+};
+
+// Resolve the node (i + di, j + dj): wraps periodic axes; returns the wall side
+// crossed (bottom/top take precedence over left/right), or -1 if inside.
+template <class C>
+__device__ __forceinline__ int resolve(const Params<C> &p, int &i, int &j)
+{
+    int wy = -1, wx = -1;
+    if (j < 0) {
+        if (p.periodic_y) j += p.ny; else wy = SIDE_BOTTOM;
+    } else if (j >= p.ny) {
+        if (p.periodic_y) j -= p.ny; else wy = SIDE_TOP;
+    }
+    if (i < 0) {
+        if (p.periodic_x) i += p.nx; else wx = SIDE_LEFT;
+    } else if (i >= p.nx) {
+        if (p.periodic_x) i -= p.nx; else wx = SIDE_RIGHT;
+    }
+    return wy >= 0 ? wy : wx;
+}
+
+// Location of canonical f_a(i, j) under each storage mode:
+//  AB      : f_a(x) = B_a(x - e_a)                    wall: B_{abar}(x) + corr
+//  AA even : f_a(x) = F_a(x)                          wall: F_a(x) + corr
+//  AA odd  : f_a(x) = F_{abar}(x - e_a)               wall: F_a(x) + corr
+template <int MODE, class C>
+__device__ __forceinline__ Loc pull_loc(const Params<C> &p, int a, int i, int j)
+{
+    int si = i - ex(a), sj = j - ey(a);
+    int side = resolve(p, si, sj);
+    Loc L;
+    L.side = side;
+    if (side >= 0) {
+        L.plane = (MODE == MODE_AB) ? opp(a) : a;
+        L.j = j;
+        L.i = i;
+    } else if (MODE == MODE_AA_EVEN) {
+        L.plane = a;
+        L.j = j;
+        L.i = i;
+    } else {
+        L.plane = (MODE == MODE_AB) ? a : opp(a);
+        L.j = sj;
+        L.i = si;
+    }
+    return L;
+}
+
+// Where the post-collision f*_a(i, j) is written by a step of each mode:
+//  AB      : B'_a(x)
+//  AA even : F_{abar}(x)
+//  AA odd  : F_a(x + e_a), or F_{abar}(x) when x + e_a lies behind a wall
+template <int MODE, class C>
+__device__ __forceinline__ Loc push_loc(const Params<C> &p, int a, int i, int j)
+{
+    Loc L;
+    L.side = -1;
+    if (MODE == MODE_AB) {
+        L.plane = a; L.j = j; L.i = i;
+    } else if (MODE == MODE_AA_EVEN) {
+        L.plane = opp(a); L.j = j; L.i = i;
+    } else {
+        int ti = i + ex(a), tj = j + ey(a);
+        int side = resolve(p, ti, tj);
+        if (side >= 0) {
+            L.plane = opp(a); L.j = j; L.i = i;
+        } else {
+            L.plane = a; L.j = tj; L.i = ti;
+        }
+    }
+    return L;
+}
+
+__device__ __forceinline__ size_t at(long long plane_elems, int pitch, int plane, int j, int i)
+{
+    return (size_t)plane * (size_t)plane_elems + (size_t)j * (size_t)pitch + (size_t)i;
+}
+
+// ---- collision ------------------------------------------------------------------
+// In:  g[a] = f_a - w_a (canonical offsets at one node).
+// Out: g[a] = f*_a - w_a (post-collision offsets).
+// Returns false when rho is not a positive finite number (divergence).
+//
+// Moments (Eq. fea-0):   rho = 1 + sum g,  j = sum e_a g_a,  u = j / rho.
+// Equilibrium offsets (Eq. feq-full):
+//   f^eq_a - w_a = w_a [ (rho - 1) + rho (3 e.u + 9/2 (e.u)^2 - 3/2 u.u) ].
+// SmrtLBM (Eq. SmrtLBM-1): with n_k = f_k - f^eq_k the indicator sum is
+//   C1 = (-n1 + n2 - n3 + n4)/4 for a in 1..4 and C2 = (-n5 + n6 - n7 + n8)/4 for
+//   a in 5..8, so with Pxx = n1 - n2 + n3 - n4 = -4 C1 and Pxy = n5 - n6 + n7 - n8 = -4 C2
+//   f*_a = f^eq_a + (-1)^a (1 - 1/tau) C = f^eq_a + s_a (1 - 1/tau)/4 P,
+//   s = (+,-,+,-) over a = 1..4 (P = Pxx) and over a = 5..8 (P = Pxy), f*_0 = f^eq_0.
+// SRT (Eq. lb.srt): f*_a = f_a - (f_a - f^eq_a) / tau.
+// Two-tau (Eq. SmrtLBM-lb.1.5): f*_a = f_a - (f_a - f^eq_a)/tau_s + s_a (1/tau_s - 1/tau)/4 P.
+template <int KIND, class C>
+__device__ __forceinline__ bool collide(const Params<C> &p, C g[9])
+{
+    const C drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+    const C rho = C(1) + drho;
+    const C jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
+    const C jy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
+    const C inv = C(1) / rho;
+    const C ux = jx * inv, uy = jy * inv;
+    const bool ok = (rho > C(0)) && (rho < C(INFINITY));
+
+    const C base = drho - C(1.5) * rho * (ux * ux + uy * uy);
+    const C r45 = C(4.5) * rho, r3 = C(3) * rho;
+    const C sp = ux + uy, sm = ux - uy;
+    const C axx = base + r45 * ux * ux, bxx = r3 * ux;
+    const C ayy = base + r45 * uy * uy, byy = r3 * uy;
+    const C app = base + r45 * sp * sp, bpp = r3 * sp;
+    const C amm = base + r45 * sm * sm, bmm = r3 * sm;
+    const C W0 = wgt<C>(0), W1 = wgt<C>(1), W5 = wgt<C>(5);
+    C q[9];
+    q[0] = W0 * base;
+    q[1] = W1 * (axx + bxx);
+    q[3] = W1 * (axx - bxx);
+    q[2] = W1 * (ayy + byy);
+    q[4] = W1 * (ayy - byy);
+    q[5] = W5 * (app + bpp);
+    q[7] = W5 * (app - bpp);
+    q[8] = W5 * (amm + bmm);
+    q[6] = W5 * (amm - bmm);
+
+    if (KIND == SMRT_COLLISION_SRT) {
+        #pragma unroll
+        for (int a = 0; a < 9; ++a) g[a] = g[a] - p.omega * (g[a] - q[a]);
+        return ok;
+    }
+    const C pxx = ((g[1] - q[1]) + (g[3] - q[3])) - ((g[2] - q[2]) + (g[4] - q[4]));
+    const C pxy = ((g[5] - q[5]) + (g[7] - q[7])) - ((g[6] - q[6]) + (g[8] - q[8]));
+    if (KIND == SMRT_COLLISION_SMRT) {
+        const C txx = p.a4 * pxx, txy = p.a4 * pxy;
+        g[0] = q[0];
+        g[1] = q[1] + txx;
+        g[3] = q[3] + txx;
+        g[2] = q[2] - txx;
+        g[4] = q[4] - txx;
+        g[5] = q[5] + txy;
+        g[7] = q[7] + txy;
+        g[6] = q[6] - txy;
+        g[8] = q[8] - txy;
+    } else {
+        const C txx = p.trt4 * pxx, txy = p.trt4 * pxy;
+        #pragma unroll
+        for (int a = 0; a < 9; ++a) g[a] = g[a] - p.omega_s * (g[a] - q[a]);
+        g[1] += txx;
+        g[3] += txx;
+        g[2] -= txx;
+        g[4] -= txx;
+        g[5] += txy;
+        g[7] += txy;
+        g[6] -= txy;
+        g[8] -= txy;
+    }
+    return ok;
+}
+
+} // namespace smrt

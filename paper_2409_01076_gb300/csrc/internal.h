@@ -1,0 +1,59 @@
+// internal.h -- shared between the C-ABI layer (api.cu) and the per-precision
+// kernel translation units (prec_*.cu).  Not part of the public interface.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "smrt.h"
+
+namespace smrt {
+
+// How the stored arrays map to the canonical f(t): the two-buffer layout, or the
+// in-place layout before an even / odd step (t even / t odd).
+enum { MODE_AB = 0, MODE_AA_EVEN = 1, MODE_AA_ODD = 2 };
+
+// Plain description of one lattice as the launchers need it.
+struct HostParams {
+    int nx, ny;
+    int pitch;          // stored elements per row
+    long long plane;    // stored elements per population plane
+    unsigned bc;
+    double tau, tau_s, u_lid;
+    int *flag;          // device divergence flag
+};
+
+// Device scratch the auxiliary launchers may use (owned by the caller).
+struct Scratch {
+    double *partials;   // >= kResidualMaxBlocks * kResidualSums doubles
+    double *sums;       // >= kResidualSums doubles
+};
+
+constexpr int kResidualSums = 5;        // |du|^2, |u1|^2, rho, rho ux, rho uy
+constexpr int kResidualMaxBlocks = 1216; // 8 x 152 SMs
+
+// Launchers of one storage precision.  `mode` is MODE_AB / MODE_AA_EVEN /
+// MODE_AA_ODD; `kind` an smrt_collision.  Field buffers (double) cover rows
+// [row0, row0 + rows) with row-major [plane][rows][nx] layout.
+struct KernelTable {
+    cudaError_t (*step)(int kind, int mode, const void *src, void *dst, const HostParams &p,
+                        cudaStream_t s);
+    cudaError_t (*get_f)(int mode, const void *state, double *f, int row0, int rows,
+                         const HostParams &p, cudaStream_t s);
+    cudaError_t (*set_f)(int mode, void *state, const double *f, int row0, int rows,
+                         const HostParams &p, cudaStream_t s);
+    cudaError_t (*init_macros)(int mode, void *state, const double *rho, const double *u,
+                               int row0, int rows, const HostParams &p, cudaStream_t s);
+    cudaError_t (*macros)(int mode, const void *state, double *rho, double *u, int row0,
+                          int rows, const HostParams &p, cudaStream_t s);
+    cudaError_t (*residual)(int kind, int mode, const void *state, const HostParams &p,
+                            const Scratch &scratch, cudaStream_t s);
+    size_t elem_bytes;
+};
+
+const KernelTable &kernels_f64();
+const KernelTable &kernels_f32();
+const KernelTable &kernels_f16();
+const KernelTable &kernels_bf16();
+
+} // namespace smrt

@@ -1,0 +1,583 @@
+// kernels.cuh -- kernel templates and launchers, instantiated once per storage
+// precision by prec_*.cu.
+//
+// Fused step (one launch per time step): every node pulls its nine canonical
+// populations f_a(x) (streaming + halfway / moving-wall bounce-back), forms the
+// moments and f^eq, applies the collision and stores f*.  Blocks come in two
+// kinds inside one grid:
+//   - interior blocks: rows 1..ny-2, columns [L, R); each thread owns VEC
+//     consecutive nodes, loads each population row with one aligned VEC-wide
+//     vector load and gets the +-1 column shift from its warp neighbour with a
+//     shuffle (one extra scalar load at each warp edge); no boundary logic;
+//   - band blocks: the remaining ring of nodes (rows 0 and ny-1, columns [0, L)
+//     and [R, nx)), one node per thread, with the full boundary resolution.
+#pragma once
+
+#include "d2q9.cuh"
+
+namespace smrt {
+
+template <class R, int VEC>
+struct alignas(sizeof(R) * VEC) RVec {
+    R v[VEC];
+};
+
+constexpr unsigned kFull = 0xffffffffu;
+
+struct StepGeom {
+    int L, R;            // interior columns [L, R), multiples of VEC
+    int bpr;             // interior blocks per row
+    int n_int_blocks;    // bpr * (ny - 2)
+    long long n_edge;    // band nodes
+};
+
+template <int VEC, int BX>
+inline StepGeom step_geom(int nx, int ny)
+{
+    StepGeom g;
+    int L = VEC < nx ? VEC : nx;
+    int R = ((nx - 1) / VEC) * VEC;
+    if (R < L) R = L;
+    g.L = L;
+    g.R = R;
+    int rows = ny - 2 > 0 ? ny - 2 : 0;
+    int cols = R;                       // threads must cover [0, R) as loaders
+    g.bpr = (R > L) ? (cols + BX * VEC - 1) / (BX * VEC) : 0;
+    g.n_int_blocks = g.bpr * rows;
+    long long bw = (long long)L + (long long)(nx - R);
+    g.n_edge = (ny >= 2 ? 2LL * nx : (long long)nx) + (long long)rows * bw;
+    return g;
+}
+
+// vals[k] = row[i0 + k + s], s in {-1, 0, +1}, for a thread owning nodes i0..i0+VEC-1.
+template <int PREC, int VEC>
+__device__ __forceinline__ void load_row(const typename Prec<PREC>::R *row, int i0, int s, int lane,
+                                         bool loader, int nx, typename Prec<PREC>::C vals[VEC])
+{
+    using P = Prec<PREC>;
+    using R = typename P::R;
+    using C = typename P::C;
+    if (VEC == 1) {
+        vals[0] = loader ? P::to_c(row[i0 + s]) : C(0);
+        return;
+    }
+    C c[VEC];
+    if (loader) {
+        RVec<R, VEC> v = *reinterpret_cast<const RVec<R, VEC> *>(row + i0);
+        #pragma unroll
+        for (int k = 0; k < VEC; ++k) c[k] = P::to_c(v.v[k]);
+    } else {
+        #pragma unroll
+        for (int k = 0; k < VEC; ++k) c[k] = C(0);
+    }
+    if (s == 0) {
+        #pragma unroll
+        for (int k = 0; k < VEC; ++k) vals[k] = c[k];
+    } else if (s < 0) {
+        C left = __shfl_up_sync(kFull, c[VEC - 1], 1);
+        if (lane == 0) left = (loader && i0 >= 1) ? P::to_c(row[i0 - 1]) : C(0);
+        vals[0] = left;
+        #pragma unroll
+        for (int k = 1; k < VEC; ++k) vals[k] = c[k - 1];
+    } else {
+        C right = __shfl_down_sync(kFull, c[0], 1);
+        if (lane == 31) right = (i0 + VEC < nx) ? P::to_c(row[i0 + VEC]) : C(0);
+        #pragma unroll
+        for (int k = 0; k < VEC - 1; ++k) vals[k] = c[k + 1];
+        vals[VEC - 1] = right;
+    }
+}
+
+// row[i0 + k + s] = vals[k]
+template <int PREC, int VEC>
+__device__ __forceinline__ void store_row(typename Prec<PREC>::R *row, int i0, int s,
+                                          const typename Prec<PREC>::C vals[VEC])
+{
+    using P = Prec<PREC>;
+    using R = typename P::R;
+    if (s == 0 && VEC > 1) {
+        RVec<R, VEC> v;
+        #pragma unroll
+        for (int k = 0; k < VEC; ++k) v.v[k] = P::to_r(vals[k]);
+        *reinterpret_cast<RVec<R, VEC> *>(row + i0) = v;
+    } else {
+        #pragma unroll
+        for (int k = 0; k < VEC; ++k) row[i0 + k + s] = P::to_r(vals[k]);
+    }
+}
+
+// One node through the full boundary resolution (band blocks, and the
+// reference behaviour every fast path must reproduce bit for bit).
+template <int PREC, int KIND, int MODE>
+__device__ __forceinline__ void step_node_generic(const typename Prec<PREC>::R *src,
+                                                  typename Prec<PREC>::R *dst,
+                                                  const Params<typename Prec<PREC>::C> &p, int i, int j)
+{
+    using P = Prec<PREC>;
+    using C = typename P::C;
+    C g[9];
+    #pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        Loc L = pull_loc<MODE>(p, a, i, j);
+        C v = P::to_c(src[at(p.plane, p.pitch, L.plane, L.j, L.i)]);
+        if (L.side >= 0) v += p.corr[L.side][a];
+        g[a] = v;
+    }
+    if (!collide<KIND>(p, g)) atomicOr(p.flag, 1);
+    #pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        Loc L = push_loc<MODE>(p, a, i, j);
+        dst[at(p.plane, p.pitch, L.plane, L.j, L.i)] = P::to_r(g[a]);
+    }
+}
+
+template <int PREC, int KIND, int MODE, int VEC, int BX>
+__global__ void __launch_bounds__(BX)
+step_kernel(const typename Prec<PREC>::R *src, typename Prec<PREC>::R *dst,
+            const Params<typename Prec<PREC>::C> p, const StepGeom geo)
+{
+    using C = typename Prec<PREC>::C;
+    const int tid = threadIdx.x;
+    const int b = blockIdx.x;
+
+    if (b >= geo.n_int_blocks) {
+        // ---- band: one node per thread, full boundary handling ----
+        long long e = (long long)(b - geo.n_int_blocks) * BX + tid;
+        if (e >= geo.n_edge) return;
+        int i, j;
+        if (e < p.nx) {
+            i = (int)e; j = 0;
+        } else if (e < 2LL * p.nx && p.ny >= 2) {
+            i = (int)(e - p.nx); j = p.ny - 1;
+        } else {
+            long long m = e - 2LL * p.nx;
+            int bw = geo.L + (p.nx - geo.R);
+            j = 1 + (int)(m / bw);
+            int k = (int)(m % bw);
+            i = k < geo.L ? k : geo.R + (k - geo.L);
+        }
+        step_node_generic<PREC, KIND, MODE>(src, dst, p, i, j);
+        return;
+    }
+
+    // ---- interior: VEC nodes per thread, no boundary logic ----
+    const int lane = tid & 31;
+    const int j = 1 + b / geo.bpr;
+    const int i0 = (b % geo.bpr) * (BX * VEC) + tid * VEC;
+    const bool active = (i0 >= geo.L) && (i0 + VEC <= geo.R);
+    const bool loader = (VEC == 1) ? active : (i0 < p.nx);
+
+    C g[VEC][9];
+    #pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        const int plane = (MODE == MODE_AA_ODD) ? opp(a) : a;
+        const int row = (MODE == MODE_AA_EVEN) ? j : j - ey(a);
+        const int s = (MODE == MODE_AA_EVEN) ? 0 : -ex(a);
+        const typename Prec<PREC>::R *rp = src + (size_t)plane * (size_t)p.plane + (size_t)row * (size_t)p.pitch;
+        C vals[VEC];
+        load_row<PREC, VEC>(rp, i0, s, lane, loader, p.nx, vals);
+        #pragma unroll
+        for (int k = 0; k < VEC; ++k) g[k][a] = vals[k];
+    }
+    bool ok = true;
+    #pragma unroll
+    for (int k = 0; k < VEC; ++k) ok &= collide<KIND>(p, g[k]);
+    if (!active) return;
+    if (!ok) atomicOr(p.flag, 1);
+    #pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        const int plane = (MODE == MODE_AA_EVEN) ? opp(a) : a;
+        const int row = (MODE == MODE_AA_ODD) ? j + ey(a) : j;
+        const int s = (MODE == MODE_AA_ODD) ? ex(a) : 0;
+        typename Prec<PREC>::R *rp = dst + (size_t)plane * (size_t)p.plane + (size_t)row * (size_t)p.pitch;
+        C vals[VEC];
+        #pragma unroll
+        for (int k = 0; k < VEC; ++k) vals[k] = g[k][a];
+        store_row<PREC, VEC>(rp, i0, s, vals);
+    }
+}
+
+// ---- state I/O and macros (one thread per node of a row chunk) -------------------
+
+template <int PREC, int MODE>
+__device__ __forceinline__ void pull_canonical(const typename Prec<PREC>::R *state,
+                                               const Params<typename Prec<PREC>::C> &p, int i, int j,
+                                               typename Prec<PREC>::C g[9])
+{
+    using P = Prec<PREC>;
+    #pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        Loc L = pull_loc<MODE>(p, a, i, j);
+        typename P::C v = P::to_c(state[at(p.plane, p.pitch, L.plane, L.j, L.i)]);
+        if (L.side >= 0) v += p.corr[L.side][a];
+        g[a] = v;
+    }
+}
+
+template <int PREC, int MODE>
+__global__ void get_f_kernel(const typename Prec<PREC>::R *state, double *f, int row0, int rows,
+                             const Params<typename Prec<PREC>::C> p)
+{
+    long long n = (long long)rows * p.nx;
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int r = (int)(t / p.nx), i = (int)(t % p.nx);
+    typename Prec<PREC>::C g[9];
+    pull_canonical<PREC, MODE>(state, p, i, row0 + r, g);
+    #pragma unroll
+    for (int a = 0; a < 9; ++a)
+        f[((size_t)a * rows + r) * p.nx + i] = (double)g[a] + wgt<double>(a);
+}
+
+template <int PREC, int MODE>
+__global__ void set_f_kernel(typename Prec<PREC>::R *state, const double *f, int row0, int rows,
+                             const Params<typename Prec<PREC>::C> p)
+{
+    using P = Prec<PREC>;
+    long long n = (long long)rows * p.nx;
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int r = (int)(t / p.nx), i = (int)(t % p.nx), j = row0 + r;
+    #pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        Loc L = pull_loc<MODE>(p, a, i, j);
+        double g = f[((size_t)a * rows + r) * p.nx + i] - wgt<double>(a);
+        if (L.side >= 0) g -= (double)p.corr[L.side][a];
+        state[at(p.plane, p.pitch, L.plane, L.j, L.i)] = P::to_r((typename P::C)g);
+    }
+}
+
+// f = f^eq(rho, u) (Eq. feq-full), written as offsets through the pull map;
+// rho == NULL selects rho = 1, u = 0.
+template <int PREC, int MODE>
+__global__ void init_macros_kernel(typename Prec<PREC>::R *state, const double *rho, const double *u,
+                                   int row0, int rows, const Params<typename Prec<PREC>::C> p)
+{
+    using P = Prec<PREC>;
+    long long n = (long long)rows * p.nx;
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int r = (int)(t / p.nx), i = (int)(t % p.nx), j = row0 + r;
+    size_t q = (size_t)r * p.nx + i;
+    double d = 1.0, ux = 0.0, uy = 0.0;           // rho == NULL: the resting state
+    if (rho) {
+        d = rho[q];
+        ux = u[q];
+        uy = u[(size_t)rows * p.nx + q];
+    }
+    double uu = ux * ux + uy * uy;
+    #pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        double eu = ex(a) * ux + ey(a) * uy;
+        double g = wgt<double>(a) * ((d - 1.0) + d * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu));
+        Loc L = pull_loc<MODE>(p, a, i, j);
+        if (L.side >= 0) g -= (double)p.corr[L.side][a];
+        state[at(p.plane, p.pitch, L.plane, L.j, L.i)] = P::to_r((typename P::C)g);
+    }
+}
+
+// Moments of Eq. (fea-0) accumulated in double from the canonical offsets.
+__device__ __forceinline__ void moments_d(const double g[9], double &rho, double &ux, double &uy)
+{
+    double drho = 0.0, jx = 0.0, jy = 0.0;
+    #pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        drho += g[a];
+        jx += ex(a) * g[a];
+        jy += ey(a) * g[a];
+    }
+    rho = 1.0 + drho;
+    ux = jx / rho;
+    uy = jy / rho;
+}
+
+template <int PREC, int MODE>
+__global__ void macros_kernel(const typename Prec<PREC>::R *state, double *rho, double *u, int row0,
+                              int rows, const Params<typename Prec<PREC>::C> p)
+{
+    long long n = (long long)rows * p.nx;
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int r = (int)(t / p.nx), i = (int)(t % p.nx);
+    typename Prec<PREC>::C g[9];
+    pull_canonical<PREC, MODE>(state, p, i, row0 + r, g);
+    double gd[9];
+    #pragma unroll
+    for (int a = 0; a < 9; ++a) gd[a] = (double)g[a];
+    double rr, ux, uy;
+    moments_d(gd, rr, ux, uy);
+    size_t q = (size_t)r * p.nx + i;
+    if (rho) rho[q] = rr;
+    if (u) {
+        u[q] = ux;
+        u[(size_t)rows * p.nx + q] = uy;
+    }
+}
+
+// ---- residual: u(t) and u(t+1) without advancing the state ------------------------
+// A block takes 32 x 8 tiles; for the tile plus a one-node halo it pulls f(t),
+// collides (the same code as the step) and keeps f* (rounded to the storage
+// format, as the step stores it) in shared memory; each tile node then pulls
+// f(t+1) from there.  Sums in double: |u1-u0|^2, |u1|^2, rho0, rho0 ux0, rho0 uy0.
+constexpr int kRTX = 32, kRTY = 8, kRHX = kRTX + 2, kRHY = kRTY + 2;
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    return v;
+}
+
+template <int PREC, int KIND, int MODE>
+__global__ void __launch_bounds__(256)
+residual_kernel(const typename Prec<PREC>::R *state, const Params<typename Prec<PREC>::C> p,
+                double *partials, int tiles_x, int tiles_y)
+{
+    using P = Prec<PREC>;
+    using R = typename P::R;
+    using C = typename P::C;
+    __shared__ R post[9][kRHY][kRHX];
+    __shared__ double u0s[3][kRTY][kRTX];
+    __shared__ double red[8][kResidualSums];
+    const int tid = threadIdx.x;
+    double acc[kResidualSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    const int ntiles = tiles_x * tiles_y;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int tx0 = (tile % tiles_x) * kRTX, ty0 = (tile / tiles_x) * kRTY;
+        for (int q = tid; q < kRHX * kRHY; q += 256) {
+            const int hx = q % kRHX, hy = q / kRHX;
+            int i = tx0 - 1 + hx, j = ty0 - 1 + hy;
+            const bool tile_node = hx >= 1 && hx <= kRTX && hy >= 1 && hy <= kRTY && i < p.nx && j < p.ny;
+            if (i > p.nx || j > p.ny) continue;
+            if (resolve(p, i, j) >= 0) continue;
+            C g[9];
+            pull_canonical<PREC, MODE>(state, p, i, j, g);
+            if (tile_node) {
+                double gd[9], rr, ux, uy;
+                #pragma unroll
+                for (int a = 0; a < 9; ++a) gd[a] = (double)g[a];
+                moments_d(gd, rr, ux, uy);
+                u0s[0][hy - 1][hx - 1] = rr;
+                u0s[1][hy - 1][hx - 1] = ux;
+                u0s[2][hy - 1][hx - 1] = uy;
+            }
+            collide<KIND>(p, g);
+            #pragma unroll
+            for (int a = 0; a < 9; ++a) post[a][hy][hx] = P::to_r(g[a]);
+        }
+        __syncthreads();
+        const int lx = tid % kRTX, ly = tid / kRTX;
+        const int i = tx0 + lx, j = ty0 + ly;
+        if (i < p.nx && j < p.ny) {
+            double g1[9];
+            #pragma unroll
+            for (int a = 0; a < 9; ++a) {
+                int si = i - ex(a), sj = j - ey(a);
+                int side = resolve(p, si, sj);
+                C v;
+                if (side >= 0) v = P::to_c(post[opp(a)][ly + 1][lx + 1]) + p.corr[side][a];
+                else v = P::to_c(post[a][ly + 1 - ey(a)][lx + 1 - ex(a)]);
+                g1[a] = (double)v;
+            }
+            double r1, ux1, uy1;
+            moments_d(g1, r1, ux1, uy1);
+            const double r0 = u0s[0][ly][lx], ux0 = u0s[1][ly][lx], uy0 = u0s[2][ly][lx];
+            const double dx = ux1 - ux0, dy = uy1 - uy0;
+            acc[0] += dx * dx + dy * dy;
+            acc[1] += ux1 * ux1 + uy1 * uy1;
+            acc[2] += r0;
+            acc[3] += r0 * ux0;
+            acc[4] += r0 * uy0;
+        }
+        __syncthreads();
+    }
+    #pragma unroll
+    for (int k = 0; k < kResidualSums; ++k) acc[k] = warp_sum(acc[k]);
+    if ((tid & 31) == 0) {
+        #pragma unroll
+        for (int k = 0; k < kResidualSums; ++k) red[tid >> 5][k] = acc[k];
+    }
+    __syncthreads();
+    if (tid < kResidualSums) {
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w) s += red[w][tid];
+        partials[(size_t)blockIdx.x * kResidualSums + tid] = s;
+    }
+}
+
+// Deterministic final sum of the per-block partials (fixed order, one block).
+static __global__ void __launch_bounds__(256) reduce_partials_kernel(const double *partials, int nblocks, double *sums)
+{
+    __shared__ double sh[kResidualSums][256];
+    const int tid = threadIdx.x;
+    double acc[kResidualSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int b = tid; b < nblocks; b += 256) {
+        #pragma unroll
+        for (int k = 0; k < kResidualSums; ++k) acc[k] += partials[(size_t)b * kResidualSums + k];
+    }
+    #pragma unroll
+    for (int k = 0; k < kResidualSums; ++k) sh[k][tid] = acc[k];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (tid < w) {
+            #pragma unroll
+            for (int k = 0; k < kResidualSums; ++k) sh[k][tid] += sh[k][tid + w];
+        }
+        __syncthreads();
+    }
+    if (tid < kResidualSums) sums[tid] = sh[tid][0];
+}
+
+// ---- launchers ---------------------------------------------------------------------
+
+template <int PREC> struct Tune;
+template <> struct Tune<SMRT_PREC_F64> { static constexpr int VEC = 2, BX = 128; };
+template <> struct Tune<SMRT_PREC_F32> { static constexpr int VEC = 4, BX = 128; };
+template <> struct Tune<SMRT_PREC_F16> { static constexpr int VEC = 8, BX = 128; };
+template <> struct Tune<SMRT_PREC_BF16> { static constexpr int VEC = 8, BX = 128; };
+
+template <int PREC, int KIND, int MODE>
+cudaError_t launch_step_km(const void *src, void *dst, const HostParams &hp, cudaStream_t s)
+{
+    using P = Prec<PREC>;
+    using R = typename P::R;
+    constexpr int VEC = Tune<PREC>::VEC, BX = Tune<PREC>::BX;
+    const Params<typename P::C> p = make_params<typename P::C>(hp);
+    const StepGeom geo = step_geom<VEC, BX>(hp.nx, hp.ny);
+    const long long edge_blocks = (geo.n_edge + BX - 1) / BX;
+    const long long blocks = (long long)geo.n_int_blocks + edge_blocks;
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    step_kernel<PREC, KIND, MODE, VEC, BX><<<(unsigned)blocks, BX, 0, s>>>(
+        (const R *)src, (R *)dst, p, geo);
+    return cudaGetLastError();
+}
+
+template <int PREC, int KIND>
+cudaError_t launch_step_k(int mode, const void *src, void *dst, const HostParams &hp, cudaStream_t s)
+{
+    switch (mode) {
+    case MODE_AB: return launch_step_km<PREC, KIND, MODE_AB>(src, dst, hp, s);
+    case MODE_AA_EVEN: return launch_step_km<PREC, KIND, MODE_AA_EVEN>(src, dst, hp, s);
+    case MODE_AA_ODD: return launch_step_km<PREC, KIND, MODE_AA_ODD>(src, dst, hp, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int PREC>
+cudaError_t launch_step(int kind, int mode, const void *src, void *dst, const HostParams &hp, cudaStream_t s)
+{
+    switch (kind) {
+    case SMRT_COLLISION_SMRT: return launch_step_k<PREC, SMRT_COLLISION_SMRT>(mode, src, dst, hp, s);
+    case SMRT_COLLISION_SRT: return launch_step_k<PREC, SMRT_COLLISION_SRT>(mode, src, dst, hp, s);
+    case SMRT_COLLISION_TWO_TAU: return launch_step_k<PREC, SMRT_COLLISION_TWO_TAU>(mode, src, dst, hp, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+inline unsigned node_blocks(int rows, int nx, int threads)
+{
+    long long n = (long long)rows * nx;
+    return (unsigned)((n + threads - 1) / threads);
+}
+
+#define SMRT_MODE_SWITCH(mode, CALL)                                  \
+    switch (mode) {                                                   \
+    case MODE_AB: { constexpr int M = MODE_AB; CALL; } break;          \
+    case MODE_AA_EVEN: { constexpr int M = MODE_AA_EVEN; CALL; } break;\
+    case MODE_AA_ODD: { constexpr int M = MODE_AA_ODD; CALL; } break;  \
+    default: return cudaErrorInvalidValue;                            \
+    }
+
+template <int PREC>
+cudaError_t launch_get_f(int mode, const void *state, double *f, int row0, int rows, const HostParams &hp,
+                         cudaStream_t s)
+{
+    using P = Prec<PREC>;
+    const Params<typename P::C> p = make_params<typename P::C>(hp);
+    if (rows <= 0) return cudaSuccess;
+    const unsigned nb = node_blocks(rows, hp.nx, 256);
+    SMRT_MODE_SWITCH(mode, (get_f_kernel<PREC, M><<<nb, 256, 0, s>>>((const typename P::R *)state, f, row0, rows, p)));
+    return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t launch_set_f(int mode, void *state, const double *f, int row0, int rows, const HostParams &hp,
+                         cudaStream_t s)
+{
+    using P = Prec<PREC>;
+    const Params<typename P::C> p = make_params<typename P::C>(hp);
+    if (rows <= 0) return cudaSuccess;
+    const unsigned nb = node_blocks(rows, hp.nx, 256);
+    SMRT_MODE_SWITCH(mode, (set_f_kernel<PREC, M><<<nb, 256, 0, s>>>((typename P::R *)state, f, row0, rows, p)));
+    return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t launch_init_macros(int mode, void *state, const double *rho, const double *u, int row0, int rows,
+                               const HostParams &hp, cudaStream_t s)
+{
+    using P = Prec<PREC>;
+    const Params<typename P::C> p = make_params<typename P::C>(hp);
+    if (rows <= 0) return cudaSuccess;
+    const unsigned nb = node_blocks(rows, hp.nx, 256);
+    SMRT_MODE_SWITCH(mode, (init_macros_kernel<PREC, M><<<nb, 256, 0, s>>>((typename P::R *)state, rho, u, row0, rows, p)));
+    return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t launch_macros(int mode, const void *state, double *rho, double *u, int row0, int rows,
+                          const HostParams &hp, cudaStream_t s)
+{
+    using P = Prec<PREC>;
+    const Params<typename P::C> p = make_params<typename P::C>(hp);
+    if (rows <= 0) return cudaSuccess;
+    const unsigned nb = node_blocks(rows, hp.nx, 256);
+    SMRT_MODE_SWITCH(mode, (macros_kernel<PREC, M><<<nb, 256, 0, s>>>((const typename P::R *)state, rho, u, row0, rows, p)));
+    return cudaGetLastError();
+}
+
+template <int PREC, int KIND>
+cudaError_t launch_residual_k(int mode, const void *state, const HostParams &hp, const Scratch &sc,
+                              cudaStream_t s)
+{
+    using P = Prec<PREC>;
+    const Params<typename P::C> p = make_params<typename P::C>(hp);
+    const int tiles_x = (hp.nx + kRTX - 1) / kRTX, tiles_y = (hp.ny + kRTY - 1) / kRTY;
+    long long nt = (long long)tiles_x * tiles_y;
+    const int nb = (int)(nt < kResidualMaxBlocks ? nt : kResidualMaxBlocks);
+    SMRT_MODE_SWITCH(mode, (residual_kernel<PREC, KIND, M><<<nb, 256, 0, s>>>((const typename P::R *)state, p,
+                                                                                 sc.partials, tiles_x, tiles_y)));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    reduce_partials_kernel<<<1, 256, 0, s>>>(sc.partials, nb, sc.sums);
+    return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t launch_residual(int kind, int mode, const void *state, const HostParams &hp, const Scratch &sc,
+                            cudaStream_t s)
+{
+    switch (kind) {
+    case SMRT_COLLISION_SMRT: return launch_residual_k<PREC, SMRT_COLLISION_SMRT>(mode, state, hp, sc, s);
+    case SMRT_COLLISION_SRT: return launch_residual_k<PREC, SMRT_COLLISION_SRT>(mode, state, hp, sc, s);
+    case SMRT_COLLISION_TWO_TAU: return launch_residual_k<PREC, SMRT_COLLISION_TWO_TAU>(mode, state, hp, sc, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int PREC>
+KernelTable make_table()
+{
+    KernelTable t;
+    t.step = &launch_step<PREC>;
+    t.get_f = &launch_get_f<PREC>;
+    t.set_f = &launch_set_f<PREC>;
+    t.init_macros = &launch_init_macros<PREC>;
+    t.macros = &launch_macros<PREC>;
+    t.residual = &launch_residual<PREC>;
+    t.elem_bytes = sizeof(typename Prec<PREC>::R);
+    return t;
+}
+
+} // namespace smrt
