@@ -46,17 +46,20 @@ def parse_args(argv=None):
                    help="steps per extra variant line (0 disables the variants)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--size", type=int, default=0,
+                   help="override the lattice side (profiling on a smaller case of the same workload)")
     return p.parse_args(argv)
 
 
-def workload(name):
+def workload(name, size=0):
     from paper_2409_01076_gb300 import workloads as W
     if name == "tgv8192":
-        return dict(name="tgv8192", nx=8192, ny=8192, tau=0.51, u_lid=0.0, bc=W.ALL_PERIODIC, u0=0.05,
-                    desc="periodic Taylor-Green vortex 8192x8192, u0=0.05, k=2pi/8192, tau=0.51")
-    n, U, re = 4096, 0.1, 1e4
-    return dict(name="cavity4096", nx=n, ny=n, tau=W.cavity_tau(n, U, re), u_lid=U, bc=W.CAVITY, u0=None,
-                desc="lid-driven cavity 4096x4096, Re=10000, U_lid=0.1, halfway bounce-back")
+        n = size or 8192
+        return dict(name="tgv%d" % n, nx=n, ny=n, tau=0.51, u_lid=0.0, bc=W.ALL_PERIODIC, u0=0.05,
+                    desc="periodic Taylor-Green vortex %dx%d, u0=0.05, k=2pi/%d, tau=0.51" % (n, n, n))
+    n, U, re = size or 4096, 0.1, 1e4
+    return dict(name="cavity%d" % n, nx=n, ny=n, tau=W.cavity_tau(n, U, re), u_lid=U, bc=W.CAVITY, u0=None,
+                desc="lid-driven cavity %dx%d, Re=10000, U_lid=0.1, halfway bounce-back" % (n, n))
 
 
 def initial_fields(wl):
@@ -167,10 +170,11 @@ def measured_hbm_peak():
 
 
 def kernel_source_hash():
+    """Hash of the sources the step kernel is compiled from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2409_01076_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
+        if name in ("d2q9.cuh", "kernels.cuh") or (name.startswith("prec_") and name.endswith(".cu")):
             with open(os.path.join(csrc, name), "rb") as fh:
                 h.update(name.encode() + b"\0" + fh.read())
     return h.hexdigest()[:16]
@@ -299,7 +303,7 @@ def reference_arm(args):
     rank, world, _ = dist_setup(args.gpus)
     if rank != 0:
         return 0
-    wl = workload(args.workload)
+    wl = workload(args.workload, args.size)
     total = args.steps + args.warmup
     side = int(math.sqrt(60.0 * ORACLE_RATE_GUESS / max(total, 1)))
     side = max(16, min(1024, side))
@@ -331,7 +335,7 @@ def gpu_arm(args):
     import paper_2409_01076_gb300 as S
 
     rank, world, local = dist_setup(args.gpus)
-    wl = workload(args.workload)
+    wl = workload(args.workload, args.size)
     nodes = wl["nx"] * wl["ny"]
     S._lib.load()
 
