@@ -155,6 +155,40 @@ SMRT_API int smrt_macros(smrt_t *h, double *rho, double *u);
  * {sum rho(t), sum rho u_x(t), sum rho u_y(t)}.  All accumulation is double. */
 SMRT_API int smrt_residual(smrt_t *h, double *r, double *sums);
 
+/* The residual of smrt_residual for a lattice the caller holds, computed
+ * without allocating any memory.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc -- for example code that
+ * runs while a framework's caching allocator owns the device memory budget
+ * (a raw cudaMalloc there can fail or fragment the pool), or latency-critical
+ * loops where cudaMalloc/cudaFree would synchronize the device -- and who
+ * therefore cannot create an smrt_t either (its state is allocated on first use).
+ *
+ * f:   the canonical f(t) in DEVICE memory of the current device,
+ *      double[9][ny][nx] (the layout of smrt_get_f); read only.
+ * out: double[4] = {r, sum rho, sum rho u_x, sum rho u_y}, host or device
+ *      memory.  r and the sums are defined as for smrt_residual, evaluated in
+ *      FP64 with the update given by tau, u_lid, bc_flags, collision and tau_s
+ *      (tau_s is read only for SMRT_COLLISION_TWO_TAU).
+ * stream: the cudaStream_t to run on (NULL: legacy default stream).  With a
+ *      device `out` the call only enqueues work; with a host `out` it waits.
+ *
+ * Scratch: the per-block partial sums live in one file-scope device array of
+ * 1216 x 5 + 4 doubles (48,672 bytes), which every GPU that loads the library
+ * holds until the process exits.  The first call on each device looks up that
+ * array's device address (cudaGetSymbolAddress) with the device current; make
+ * that first call before any stream capture.  Every call on a device shares the
+ * array and leaves its contents behind; nothing in it needs to start at zero
+ * (each call writes every slot it later reads).  Calls whose work overlaps on
+ * the GPU -- on different streams, or from different host threads -- race on
+ * the array: serialise them.
+ * Limits: nx, ny >= 2 and nx * ny <= SMRT_NOALLOC_MAX_NODES; larger lattices
+ * return SMRT_ERR_ARG.  Errors are reported through smrt_last_error(NULL).
+ * Calls no cudaMalloc, cudaFree or other allocating routine. */
+#define SMRT_NOALLOC_MAX_NODES (1LL << 30)
+SMRT_API int smrt_residual_noalloc(const double *f, int nx, int ny, double tau, double u_lid,
+                                   unsigned bc_flags, int collision, double tau_s, double *out,
+                                   void *stream);
+
 /* Copy the canonical state f(t) out as double[9][ny][nx]. */
 SMRT_API int smrt_get_f(smrt_t *h, double *f);
 

@@ -128,6 +128,31 @@ def smrt_residual(h: Handle) -> tuple[float, tuple[float, float, float]]:
     return r.value, (sums[0], sums[1], sums[2])
 
 
+def smrt_residual_noalloc(f, tau: float, u_lid: float = 0.0, bc: int = CAVITY,
+                          collision: int = SMRT_COLLISION_SMRT, tau_s: float = 1.0, out=None,
+                          stream=None):
+    """Residual of a caller-held canonical field, allocating nothing on the device.
+
+    For callers that cannot call cudaMalloc (and so cannot create a handle):
+    f is a CUDA float64 tensor (9, ny, nx) holding f(t).  `out` may be a CUDA
+    float64 tensor of 4 elements (the call then only enqueues work) or None, in
+    which case the call waits and returns (r, (sum rho, sum rho ux, sum rho uy)).
+    """
+    import numpy as np
+    _, ny, nx = tuple(f.shape)
+    fp = _ptr(f, (9, ny, nx), "f", False)
+    raw = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
+    host = out is None
+    res = np.empty(4) if host else out
+    rc = _lib.load().smrt_residual_noalloc(fp, nx, ny, tau, u_lid, bc, collision, tau_s,
+                                           _ptr(res, (4,), "out", True), ctypes.c_void_p(raw))
+    if rc != SMRT_OK:
+        raise SmrtError(rc, smrt_last_error(None))
+    if host:
+        return float(res[0]), (float(res[1]), float(res[2]), float(res[3]))
+    return None
+
+
 def smrt_get_f(h: Handle, f) -> None:
     _check(_lib.load().smrt_get_f(h, _ptr(f, (9, h.ny, h.nx), "f", True)), h)
 

@@ -27,6 +27,8 @@ SIGNATURES = [
     ("smrt_sync", c_int, [c_void_p]),
     ("smrt_macros", c_int, [c_void_p, c_void_p, c_void_p]),
     ("smrt_residual", c_int, [c_void_p, c_void_p, c_void_p]),
+    ("smrt_residual_noalloc", c_int, [c_void_p, c_int, c_int, c_double, c_double, c_uint, c_int, c_double,
+                                      c_void_p, c_void_p]),
     ("smrt_get_f", c_int, [c_void_p, c_void_p]),
     ("smrt_set_f", c_int, [c_void_p, c_void_p]),
     ("smrt_init_macros", c_int, [c_void_p, c_void_p, c_void_p]),

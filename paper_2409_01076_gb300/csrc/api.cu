@@ -86,6 +86,17 @@ int cuda_fail(smrt_t *h, cudaError_t e, const char *what)
     return fail(h, SMRT_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
 }
 
+} // namespace
+
+namespace smrt {
+void set_thread_error(const char *msg)
+{
+    g_create_error = msg;
+}
+} // namespace smrt
+
+namespace {
+
 #define CUDA_TRY(h, call)                                  \
     do {                                                   \
         cudaError_t e_ = (call);                           \

@@ -56,4 +56,8 @@ const KernelTable &kernels_f32();
 const KernelTable &kernels_f16();
 const KernelTable &kernels_bf16();
 
+// Records the message smrt_last_error(NULL) returns on the calling thread
+// (entry points that take no handle report their errors here).
+void set_thread_error(const char *msg);
+
 } // namespace smrt
