@@ -48,6 +48,10 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--size", type=int, default=0,
                    help="override the lattice side (profiling on a smaller case of the same workload)")
+    p.add_argument("--report", choices=["", "precision"], default="",
+                   help="precision: 16-bit vs FP32 storage throughput and error report (its own JSON line)")
+    p.add_argument("--oracle-steps", type=int, default=200)
+    p.add_argument("--long-steps", type=int, default=20000)
     return p.parse_args(argv)
 
 
@@ -414,10 +418,84 @@ def gpu_arm(args):
     return 0
 
 
+def _oracle_cavity_u(n, re, steps):
+    """FP64 oracle: u after `steps` updates of an n x n cavity (U_lid = 0.1) at Reynolds number re."""
+    import oracle as O
+    from paper_2409_01076_gb300 import workloads as W
+    tau = W.cavity_tau(n, 0.1, re)
+    f = O.run(O.cavity_initial(n, n), steps, O.CAVITY, tau, u_lid=0.1)
+    return O.macros(f)[1]
+
+
+def precision_report(args):
+    """16-bit offset storage vs FP32 storage: throughput on 8192^2 cavities at Re 5000 / 20000, and
+    velocity error of each storage format on the 1024^2 cavity at the same Re, against the FP64
+    oracle (short horizon) and against the FP64 GPU path (long horizon)."""
+    import multiprocessing as mp
+    import numpy as np
+    n_err, s_oracle, s_long = 1024, args.oracle_steps, args.long_steps
+    res_list = (5000.0, 20000.0)
+    # the oracle runs in spawned processes, started before this process touches CUDA
+    pool = mp.get_context("spawn").Pool(len(res_list))
+    pending = {re: pool.apply_async(_oracle_cavity_u, (n_err, re, s_oracle)) for re in res_list}
+    pool.close()
+
+    import torch
+    import paper_2409_01076_gb300 as S
+    from paper_2409_01076_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    S._lib.load()
+    precs = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
+
+    def gpu_u(n, re, steps, prec, layout=0):
+        h = S.smrt_create(n, n, W.cavity_tau(n, 0.1, re), 0.1, W.CAVITY)
+        S.smrt_set_option(h, S.SMRT_OPT_PRECISION, precs[prec])
+        S.smrt_set_option(h, S.SMRT_OPT_LAYOUT, layout)
+        S.smrt_step(h, steps)
+        rho = np.empty((n, n))
+        u = np.empty((2, n, n))
+        S.smrt_macros(h, rho, u)
+        S.smrt_destroy(h)
+        return u
+
+    out = {"report": "precision", "unit_error": "velocity error / U_lid", "U_lid": 0.1, "error_lattice": n_err,
+           "oracle_steps": s_oracle, "long_steps": s_long, "by_re": {}}
+    for re in res_list:
+        entry = {"tau_1024": W.cavity_tau(n_err, 0.1, re), "tau_8192": W.cavity_tau(8192, 0.1, re)}
+        # throughput on the 8192^2 cavity
+        wl = dict(name="cavity8192", nx=8192, ny=8192, tau=W.cavity_tau(8192, 0.1, re), u_lid=0.1, bc=W.CAVITY,
+                  u0=None, desc="")
+        thr = {}
+        for prec in ("f32", "f16", "bf16"):
+            for layout in ("ab", "aa"):
+                thr["%s-%s" % (prec, layout)] = run_variant(S, wl, None, None, prec, layout, "smrt",
+                                                            args.variant_steps or 1000, 10, 1)
+        entry["throughput_8192"] = thr
+        u64_long = gpu_u(n_err, re, s_long, "f64")
+        long_err = {}
+        for prec in ("f32", "f16", "bf16"):
+            d = gpu_u(n_err, re, s_long, prec) - u64_long
+            long_err[prec] = {"max": float(np.abs(d).max() / 0.1), "rms": float(np.sqrt((d * d).mean()) / 0.1)}
+        entry["error_vs_gpu_f64_long"] = long_err
+        entry["gpu_f64_speed_max"] = float(np.abs(u64_long).max())
+        u_ref = pending[re].get()
+        short_err = {}
+        for prec in ("f64", "f32", "f16", "bf16"):
+            d = gpu_u(n_err, re, s_oracle, prec) - u_ref
+            short_err[prec] = {"max": float(np.abs(d).max() / 0.1), "rms": float(np.sqrt((d * d).mean()) / 0.1)}
+        entry["error_vs_oracle"] = short_err
+        out["by_re"]["%d" % re] = entry
+    pool.join()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return reference_arm(args)
+    if args.report == "precision":
+        return precision_report(args)
     return gpu_arm(args)
 
 
