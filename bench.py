@@ -48,8 +48,14 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--size", type=int, default=0,
                    help="override the lattice side (profiling on a smaller case of the same workload)")
-    p.add_argument("--report", choices=["", "precision"], default="",
-                   help="precision: 16-bit vs FP32 storage throughput and error report (its own JSON line)")
+    p.add_argument("--report", choices=["", "precision", "batched"], default="",
+                   help="precision: 16-bit vs FP32 storage report; batched: 512 cavities to steady state "
+                        "(each prints its own JSON line)")
+    p.add_argument("--tol", type=float, default=1e-7)
+    p.add_argument("--residual", choices=["stride", "step"], default="stride",
+                   help="batched report: stride (mean change per update over a check) or one-step residual")
+    p.add_argument("--check-every", type=int, default=500)
+    p.add_argument("--max-steps", type=int, default=200000)
     p.add_argument("--oracle-steps", type=int, default=200)
     p.add_argument("--long-steps", type=int, default=20000)
     return p.parse_args(argv)
@@ -400,6 +406,7 @@ def gpu_arm(args):
             for layout, kind in [("ab", "smrt"), ("ab", "srt"), ("aa", "smrt")]:
                 variants["cavity4096-f32-%s-%s" % (layout, kind)] = run_variant(
                     S, cav, None, None, "f32", layout, kind, vs, 10, world)
+            variants["batched512-f32-ab-smrt"] = batched_throughput(S, max(vs // 10, 20))
         result["variants"] = variants
 
     del rho_d, u_d
@@ -415,6 +422,77 @@ def gpu_arm(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+    return 0
+
+
+def batched_setup(S, count=512, seed=0, layout="ab"):
+    """The seeded uneven batch: sides uniform over {64..1024}, Re log-uniform in [100, 5000], U_lid = 0.1."""
+    from paper_2409_01076_gb300 import workloads as W
+    cav = W.batched_cavities(count, seed)
+    nx = [n for n, _ in cav]
+    taus = [W.cavity_tau(n, 0.1, re) for n, re in cav]
+    b = S.smrt_batch_create(nx, nx, taus, [0.1] * count, W.CAVITY, S.SMRT_PREC_F32,
+                            {"ab": 0, "aa": 1}[layout], S.SMRT_COLLISION_SMRT)
+    return b, cav
+
+
+def batched_throughput(S, steps, layout="ab"):
+    import torch
+    b, cav = batched_setup(S, layout=layout)
+    nodes = S.smrt_batch_nodes(b)
+    choice = S.smrt_batch_autotune(b, 10)
+    S.smrt_batch_step(b, 4)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    S.smrt_batch_step(b, steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    S.smrt_batch_destroy(b)
+    return {"mlups": round(nodes * steps / (ms * 1e-3) / 1e6, 1), "ms_per_step": round(ms / steps, 5),
+            "hbm_gbs": round(72 * nodes / (ms / steps * 1e-3) / 1e9, 1), "steps": steps, "cavities": len(cav),
+            "nodes": nodes, "tile_shape_choice": choice, "layout": layout}
+
+
+def batched_report(args):
+    """512 uneven cavities (seed 0) run to stride residual 1e-7 in one batch, with a step cap."""
+    import numpy as np
+    import torch
+    import paper_2409_01076_gb300 as S
+    torch.cuda.set_device(0)
+    S._lib.load()
+    b, cav = batched_setup(S, layout=args.layout)
+    nodes = S.smrt_batch_nodes(b)
+    t0 = time.perf_counter()
+    choice = S.smrt_batch_autotune(b, 10)
+    t1 = time.perf_counter()
+    kind = S.SMRT_BATCH_RESIDUAL_STRIDE if args.residual == "stride" else S.SMRT_BATCH_RESIDUAL_STEP
+    S.smrt_batch_run(b, args.tol, args.check_every, args.max_steps, kind)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    steps, res, state = S.smrt_batch_status(b)
+    node_steps = sum(n * n * int(s) for (n, _), s in zip(cav, steps))
+    out = {"report": "batched", "cavities": len(cav), "nodes": nodes, "tol": args.tol, "residual": args.residual,
+           "check_every": args.check_every, "max_steps": args.max_steps, "layout": args.layout,
+           "tile_shape_choice": choice, "autotune_s": round(t1 - t0, 3), "run_s": round(t2 - t1, 3),
+           "node_updates": node_steps, "mlups_effective": round(node_steps / (t2 - t1) / 1e6, 1),
+           "converged": int((state == S.SMRT_BATCH_CONVERGED).sum()),
+           "capped": int((state == S.SMRT_BATCH_CAPPED).sum()),
+           "diverged": int((state == S.SMRT_BATCH_DIVERGED).sum()),
+           "by_side": {}}
+    for side in sorted(set(n for n, _ in cav)):
+        idx = [k for k, (n, _) in enumerate(cav) if n == side]
+        conv = [k for k in idx if state[k] == S.SMRT_BATCH_CONVERGED]
+        out["by_side"][str(side)] = {
+            "count": len(idx), "converged": len(conv),
+            "steps_median": float(np.median([steps[k] for k in conv])) if conv else None,
+            "steps_max": int(max(steps[k] for k in conv)) if conv else None,
+            "final_residual_quartiles": [float(np.quantile([res[k] for k in idx], q)) for q in (0.0, 0.25, 0.5,
+                                                                                              0.75, 1.0)],
+            "re_range": [round(min(cav[k][1] for k in idx), 1), round(max(cav[k][1] for k in idx), 1)]}
+    S.smrt_batch_destroy(b)
+    print(json.dumps(out), flush=True)
     return 0
 
 
@@ -496,6 +574,8 @@ def main(argv=None):
         return reference_arm(args)
     if args.report == "precision":
         return precision_report(args)
+    if args.report == "batched":
+        return batched_report(args)
     return gpu_arm(args)
 
 

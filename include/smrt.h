@@ -219,6 +219,80 @@ SMRT_API const char *smrt_last_error(const smrt_t *h);
 /* Free the handle's device memory and the handle.  NULL is ignored. */
 SMRT_API void smrt_destroy(smrt_t *h);
 
+/* ---- batches of independent lattices ------------------------------------------
+ * Many lattices ("cavities") of uneven size and relaxation time, advanced by the
+ * same update as smrt_step (bit for bit: the same per-block kernel code) in one
+ * launch per step: a persistent work-list kernel walks the step blocks of every
+ * active lattice.  Lattice k has nx[k] x ny[k] nodes, tau[k], u_lid[k]; all share
+ * bc_flags, the collision kind (SMRT or SRT), the precision (F32 or F64) and the
+ * layout.  Each lattice starts at f = f^eq(1, 0), t = 0.  Lattices retire
+ * (stop advancing) in smrt_batch_run when converged, capped or diverged.
+ * The paper runs one cavity at a time; batching is this library's addition. */
+typedef struct smrt_batch_t smrt_batch_t;
+enum smrt_batch_state {
+    SMRT_BATCH_ACTIVE = 0, SMRT_BATCH_CONVERGED = 1, SMRT_BATCH_CAPPED = 2, SMRT_BATCH_DIVERGED = 3
+};
+
+/* Allocates all lattices in one buffer (two for the AB layout) on the current
+ * device.  Host arrays of length count.  Errors: SMRT_ERR_ARG (invalid sizes,
+ * tau <= 0.5, |u_lid| >= 1/sqrt(3), flags, precision other than F32/F64,
+ * collision other than SMRT/SRT), SMRT_ERR_OOM; message in smrt_last_error(NULL). */
+SMRT_API int smrt_batch_create(int count, const int *nx, const int *ny, const double *tau, const double *u_lid,
+                               unsigned bc_flags, int precision, int layout, int collision, smrt_batch_t **out);
+
+/* Stream for every later launch and copy (NULL: legacy default stream). */
+SMRT_API int smrt_batch_set_stream(smrt_batch_t *b, void *stream);
+
+/* Times each candidate tile shape (nodes per thread x threads per block) of the
+ * work-list kernel on `steps` steps of this batch, run on a copy of the state so
+ * no lattice advances, and keeps the fastest; *choice (may be NULL) receives its
+ * index.  Allocates one scratch copy of the populations for the duration. */
+SMRT_API int smrt_batch_autotune(smrt_batch_t *b, int steps, int *choice);
+
+/* n >= 0 updates of every active lattice (one work-list launch each); waits,
+ * then marks lattices whose divergence word is set as SMRT_BATCH_DIVERGED. */
+SMRT_API int smrt_batch_step(smrt_batch_t *b, long long n);
+
+/* Runs until no lattice is active: replays a CUDA graph of check_every updates
+ * (rounded up to even) plus a residual pass, then retires each active lattice
+ * whose residual r_k is below tol (CONVERGED), that reached max_steps (CAPPED),
+ * or whose divergence word is set or r_k is not finite (DIVERGED).
+ * residual_kind SMRT_BATCH_RESIDUAL_STEP: the one-step residual of smrt_residual,
+ *   r_k = ||u(t+1) - u(t)||_2 / ||u(t+1)||_2 at the last update of each chunk.
+ * residual_kind SMRT_BATCH_RESIDUAL_STRIDE: the mean change per update over the
+ *   chunk, r_k = ||u(t) - u(t - check_every)||_2 / (check_every ||u(t)||_2); the
+ *   first check of a run compares with zero velocity.  With FP32 storage the
+ *   one-step residual stops falling near 1e-7..1e-6 (rounding), and a period-two
+ *   oscillation that halfway bounce-back keeps alive at the lid corners can hold
+ *   it near 1e-5; the even stride averages both out.
+ * *n_active (may be NULL) receives the active count at return (0). */
+enum smrt_batch_residual { SMRT_BATCH_RESIDUAL_STEP = 0, SMRT_BATCH_RESIDUAL_STRIDE = 1 };
+SMRT_API int smrt_batch_run(smrt_batch_t *b, double tol, long long check_every, long long max_steps,
+                            int residual_kind, int *n_active);
+
+/* Per-lattice host arrays of length count (each may be NULL): updates applied,
+ * last residual of smrt_batch_run (-1 before the first check), smrt_batch_state. */
+SMRT_API int smrt_batch_status(const smrt_batch_t *b, long long *steps, double *residual, int *state);
+
+/* Canonical f(t) of lattice k as double[9][ny][nx] (host or device memory). */
+SMRT_API int smrt_batch_get_f(smrt_batch_t *b, int k, double *f);
+
+/* rho(t), u(t) of lattice k: double[ny][nx] and double[2][ny][nx], host or device. */
+SMRT_API int smrt_batch_macros(smrt_batch_t *b, int k, double *rho, double *u);
+
+/* f = f^eq(rho, u) in lattice k (a warm start); only while k is active and in step
+ * with the others.  rho, u: host or device, as in smrt_init_macros. */
+SMRT_API int smrt_batch_init_macros(smrt_batch_t *b, int k, const double *rho, const double *u);
+
+/* Total nodes of the batch (-1 for NULL). */
+SMRT_API long long smrt_batch_nodes(const smrt_batch_t *b);
+
+/* Last error message of b (of the thread's last failed create when b is NULL). */
+SMRT_API const char *smrt_batch_last_error(const smrt_batch_t *b);
+
+/* Frees the batch.  NULL is ignored. */
+SMRT_API void smrt_batch_destroy(smrt_batch_t *b);
+
 #ifdef __cplusplus
 }
 #endif

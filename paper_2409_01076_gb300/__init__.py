@@ -187,3 +187,115 @@ def smrt_destroy(h: Handle) -> None:
     if h is not None and h.ptr and h.ptr.value:
         _lib.load().smrt_destroy(h.ptr)
         h.ptr = ctypes.c_void_p()
+
+
+# ---- batches of independent lattices ------------------------------------------------
+
+SMRT_BATCH_ACTIVE, SMRT_BATCH_CONVERGED, SMRT_BATCH_CAPPED, SMRT_BATCH_DIVERGED = 0, 1, 2, 3
+
+
+class BatchHandle:
+    """An smrt_batch_t* with the per-lattice sizes; destroyed when garbage-collected."""
+
+    def __init__(self, ptr: int, nx, ny):
+        self.ptr = ctypes.c_void_p(ptr)
+        self.nx, self.ny = list(nx), list(ny)
+        self.count = len(self.nx)
+
+    def __del__(self):
+        try:
+            smrt_batch_destroy(self)
+        except Exception:
+            pass
+
+    @property
+    def _as_parameter_(self):
+        return self.ptr
+
+
+def _bcheck(rc: int, b) -> None:
+    if rc != SMRT_OK:
+        raise SmrtError(rc, smrt_batch_last_error(b))
+
+
+def smrt_batch_create(nx, ny, tau, u_lid, bc: int = CAVITY, precision: int = SMRT_PREC_F32,
+                      layout: int = SMRT_LAYOUT_AB, collision: int = SMRT_COLLISION_SMRT) -> BatchHandle:
+    import numpy as np
+    n = len(nx)
+    if not (len(ny) == len(tau) == len(u_lid) == n):
+        raise ValueError("nx, ny, tau, u_lid must have the same length")
+    anx = np.ascontiguousarray(nx, dtype=np.int32)
+    any_ = np.ascontiguousarray(ny, dtype=np.int32)
+    atau = np.ascontiguousarray(tau, dtype=np.float64)
+    au = np.ascontiguousarray(u_lid, dtype=np.float64)
+    out = ctypes.c_void_p()
+    rc = _lib.load().smrt_batch_create(n, anx.ctypes.data, any_.ctypes.data, atau.ctypes.data, au.ctypes.data,
+                                       bc, precision, layout, collision, ctypes.byref(out))
+    if rc != SMRT_OK:
+        raise SmrtError(rc, smrt_batch_last_error(None))
+    return BatchHandle(out.value, anx.tolist(), any_.tolist())
+
+
+def smrt_batch_set_stream(b: BatchHandle, stream=None) -> None:
+    raw = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
+    _bcheck(_lib.load().smrt_batch_set_stream(b, ctypes.c_void_p(raw)), b)
+
+
+def smrt_batch_autotune(b: BatchHandle, steps: int = 10) -> int:
+    choice = ctypes.c_int(-1)
+    _bcheck(_lib.load().smrt_batch_autotune(b, int(steps), ctypes.byref(choice)), b)
+    return choice.value
+
+
+def smrt_batch_step(b: BatchHandle, n: int) -> None:
+    _bcheck(_lib.load().smrt_batch_step(b, int(n)), b)
+
+
+SMRT_BATCH_RESIDUAL_STEP, SMRT_BATCH_RESIDUAL_STRIDE = 0, 1
+
+
+def smrt_batch_run(b: BatchHandle, tol: float, check_every: int, max_steps: int,
+                   residual_kind: int = SMRT_BATCH_RESIDUAL_STEP) -> int:
+    n_active = ctypes.c_int(-1)
+    _bcheck(_lib.load().smrt_batch_run(b, float(tol), int(check_every), int(max_steps), int(residual_kind),
+                                       ctypes.byref(n_active)), b)
+    return n_active.value
+
+
+def smrt_batch_status(b: BatchHandle):
+    """Returns (steps[count] int64, residual[count] float64, state[count] int32)."""
+    import numpy as np
+    steps = np.empty(b.count, dtype=np.int64)
+    res = np.empty(b.count, dtype=np.float64)
+    state = np.empty(b.count, dtype=np.int32)
+    _bcheck(_lib.load().smrt_batch_status(b, steps.ctypes.data, res.ctypes.data, state.ctypes.data), b)
+    return steps, res, state
+
+
+def smrt_batch_get_f(b: BatchHandle, k: int, f) -> None:
+    _bcheck(_lib.load().smrt_batch_get_f(b, int(k), _ptr(f, (9, b.ny[k], b.nx[k]), "f", True)), b)
+
+
+def smrt_batch_macros(b: BatchHandle, k: int, rho, u) -> None:
+    _bcheck(_lib.load().smrt_batch_macros(b, int(k), _ptr(rho, (b.ny[k], b.nx[k]), "rho", True),
+                                          _ptr(u, (2, b.ny[k], b.nx[k]), "u", True)), b)
+
+
+def smrt_batch_init_macros(b: BatchHandle, k: int, rho, u) -> None:
+    _bcheck(_lib.load().smrt_batch_init_macros(b, int(k), _ptr(rho, (b.ny[k], b.nx[k]), "rho", False),
+                                               _ptr(u, (2, b.ny[k], b.nx[k]), "u", False)), b)
+
+
+def smrt_batch_nodes(b: BatchHandle) -> int:
+    return int(_lib.load().smrt_batch_nodes(b))
+
+
+def smrt_batch_last_error(b) -> str:
+    raw = _lib.load().smrt_batch_last_error(b if b is not None else None)
+    return raw.decode() if raw else ""
+
+
+def smrt_batch_destroy(b: BatchHandle) -> None:
+    if b is not None and b.ptr and b.ptr.value:
+        _lib.load().smrt_batch_destroy(b.ptr)
+        b.ptr = ctypes.c_void_p()

@@ -37,6 +37,19 @@ SIGNATURES = [
     ("smrt_device_bytes", c_size_t, [c_void_p]),
     ("smrt_last_error", c_char_p, [c_void_p]),
     ("smrt_destroy", None, [c_void_p]),
+    ("smrt_batch_create", c_int, [c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_uint, c_int, c_int, c_int,
+                                  ctypes.POINTER(c_void_p)]),
+    ("smrt_batch_set_stream", c_int, [c_void_p, c_void_p]),
+    ("smrt_batch_autotune", c_int, [c_void_p, c_int, ctypes.POINTER(c_int)]),
+    ("smrt_batch_step", c_int, [c_void_p, c_longlong]),
+    ("smrt_batch_run", c_int, [c_void_p, c_double, c_longlong, c_longlong, c_int, ctypes.POINTER(c_int)]),
+    ("smrt_batch_status", c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("smrt_batch_get_f", c_int, [c_void_p, c_int, c_void_p]),
+    ("smrt_batch_macros", c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    ("smrt_batch_init_macros", c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    ("smrt_batch_nodes", c_longlong, [c_void_p]),
+    ("smrt_batch_last_error", c_char_p, [c_void_p]),
+    ("smrt_batch_destroy", None, [c_void_p]),
 ]
 
 

@@ -68,7 +68,11 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + ".tmp.%d" % os.getpid()
-    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lrt", "-lpthread", "-ldl"]
+    exports = os.path.join(BUILD, "exports.map")       # export the C ABI only
+    with open(exports, "w") as fh:
+        fh.write("{ global: smrt_*; local: *; };\n")
+    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-Xlinker", "--version-script=" + exports,
+           "-lcudart_static", "-lrt", "-lpthread", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))

@@ -179,14 +179,14 @@ __device__ __forceinline__ void step_node_generic(const typename Prec<PREC>::R *
     }
 }
 
+// Block b of one lattice's step grid (interior block or band block), executed
+// by all BX threads of the calling block.
 template <int PREC, int KIND, int MODE, int VEC, int BX>
-__global__ void __launch_bounds__(BX)
-step_kernel(const typename Prec<PREC>::R *src, typename Prec<PREC>::R *dst,
-            const Params<typename Prec<PREC>::C> p, const StepGeom geo)
+__device__ __forceinline__ void step_block(const typename Prec<PREC>::R *src, typename Prec<PREC>::R *dst,
+                                           const Params<typename Prec<PREC>::C> &p, const StepGeom &geo, int b)
 {
     using C = typename Prec<PREC>::C;
     const int tid = threadIdx.x;
-    const int b = blockIdx.x;
 
     if (b >= geo.n_int_blocks) {
         // ---- band: one node per thread, full boundary handling ----
@@ -244,6 +244,14 @@ step_kernel(const typename Prec<PREC>::R *src, typename Prec<PREC>::R *dst,
         for (int k = 0; k < VEC; ++k) vals[k] = g[k][a];
         store_row<PREC, VEC>(rp, i0, s, lane, active, vals);
     }
+}
+
+template <int PREC, int KIND, int MODE, int VEC, int BX>
+__global__ void __launch_bounds__(BX)
+step_kernel(const typename Prec<PREC>::R *src, typename Prec<PREC>::R *dst,
+            const Params<typename Prec<PREC>::C> p, const StepGeom geo)
+{
+    step_block<PREC, KIND, MODE, VEC, BX>(src, dst, p, geo, blockIdx.x);
 }
 
 // ---- state I/O and macros (one thread per node of a row chunk) -------------------
