@@ -48,9 +48,11 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--size", type=int, default=0,
                    help="override the lattice side (profiling on a smaller case of the same workload)")
-    p.add_argument("--report", choices=["", "precision", "batched"], default="",
+    p.add_argument("--report", choices=["", "precision", "batched", "batched-throughput"], default="",
                    help="precision: 16-bit vs FP32 storage report; batched: 512 cavities to steady state "
                         "(each prints its own JSON line)")
+    p.add_argument("--batch-count", type=int, default=512)
+    p.add_argument("--batch-sides", default="64,128,256,512,1024")
     p.add_argument("--tol", type=float, default=1e-7)
     p.add_argument("--residual", choices=["stride", "step"], default="stride",
                    help="batched report: stride (mean change per update over a check) or one-step residual")
@@ -425,10 +427,10 @@ def gpu_arm(args):
     return 0
 
 
-def batched_setup(S, count=512, seed=0, layout="ab"):
+def batched_setup(S, count=512, seed=0, layout="ab", sides=(64, 128, 256, 512, 1024)):
     """The seeded uneven batch: sides uniform over {64..1024}, Re log-uniform in [100, 5000], U_lid = 0.1."""
     from paper_2409_01076_gb300 import workloads as W
-    cav = W.batched_cavities(count, seed)
+    cav = W.batched_cavities(count, seed, sides=tuple(sides))
     nx = [n for n, _ in cav]
     taus = [W.cavity_tau(n, 0.1, re) for n, re in cav]
     b = S.smrt_batch_create(nx, nx, taus, [0.1] * count, W.CAVITY, S.SMRT_PREC_F32,
@@ -436,9 +438,9 @@ def batched_setup(S, count=512, seed=0, layout="ab"):
     return b, cav
 
 
-def batched_throughput(S, steps, layout="ab"):
+def batched_throughput(S, steps, layout="ab", count=512, sides=(64, 128, 256, 512, 1024)):
     import torch
-    b, cav = batched_setup(S, layout=layout)
+    b, cav = batched_setup(S, count=count, layout=layout, sides=sides)
     nodes = S.smrt_batch_nodes(b)
     choice = S.smrt_batch_autotune(b, 10)
     S.smrt_batch_step(b, 4)
@@ -462,7 +464,7 @@ def batched_report(args):
     import paper_2409_01076_gb300 as S
     torch.cuda.set_device(0)
     S._lib.load()
-    b, cav = batched_setup(S, layout=args.layout)
+    b, cav = batched_setup(S, count=args.batch_count, layout=args.layout, sides=_sides(args))
     nodes = S.smrt_batch_nodes(b)
     t0 = time.perf_counter()
     choice = S.smrt_batch_autotune(b, 10)
@@ -576,7 +578,20 @@ def main(argv=None):
         return precision_report(args)
     if args.report == "batched":
         return batched_report(args)
+    if args.report == "batched-throughput":
+        import torch
+        import paper_2409_01076_gb300 as S
+        torch.cuda.set_device(0)
+        S._lib.load()
+        out = batched_throughput(S, args.steps, args.layout, args.batch_count, _sides(args))
+        out["report"] = "batched-throughput"
+        print(json.dumps(out), flush=True)
+        return 0
     return gpu_arm(args)
+
+
+def _sides(args):
+    return tuple(int(s) for s in args.batch_sides.split(","))
 
 
 if __name__ == "__main__":
