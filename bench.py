@@ -48,9 +48,13 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--size", type=int, default=0,
                    help="override the lattice side (profiling on a smaller case of the same workload)")
-    p.add_argument("--report", choices=["", "precision", "batched", "batched-throughput"], default="",
+    p.add_argument("--report", choices=["", "precision", "batched", "batched-throughput", "learned"], default="",
                    help="precision: 16-bit vs FP32 storage report; batched: 512 cavities to steady state "
                         "(each prints its own JSON line)")
+    p.add_argument("--learned-count", type=int, default=2000)
+    p.add_argument("--learned-iters", type=int, default=2000)
+    p.add_argument("--learned-cap", type=int, default=150000)
+    p.add_argument("--learned-cap-1024", type=int, default=1000000)
     p.add_argument("--batch-count", type=int, default=512)
     p.add_argument("--batch-sides", default="64,128,256,512,1024")
     p.add_argument("--tol", type=float, default=1e-7)
@@ -498,6 +502,45 @@ def batched_report(args):
     return 0
 
 
+def learned_report(args):
+    """U-Net warm start: solver-generated steady 256^2 cavities (Re log-uniform in [100, 1e4]), training on
+    the GPU with libsmrt's NN kernels, then time-to-steady (stride residual 1e-7) cold vs warm on held-out Re
+    at 256^2 and 1024^2."""
+    import numpy as np
+    import torch
+    import paper_2409_01076_gb300 as S
+    from paper_2409_01076_gb300 import warmstart as WS
+    from paper_2409_01076_gb300.unet import UNet
+    torch.cuda.set_device(0)
+    S._lib.load()
+    out = {"report": "learned", "U_lid": WS.U_LID, "tol": args.tol, "residual": "stride"}
+    res_train = WS.sample_res(args.learned_count, seed=1)
+    targets, info = WS.generate_dataset(res_train, 256, args.tol, 1000, args.learned_cap)
+    out["dataset"] = info
+    net = UNet(base=32, seed=0)
+    out["params"] = net.n_params()
+    hist, train_s = WS.train(net, res_train, targets, iters=args.learned_iters, batch=16, lr=2e-3)
+    out["training"] = {"iters": args.learned_iters, "batch": 16, "seconds": round(train_s, 2),
+                       "loss_first_last": [hist[0][1], hist[-1][1]], "loss_history": hist[::4],
+                       "final_loss_scale": net.grad_scale}
+    del targets
+    torch.cuda.empty_cache()
+    held_out = [130.0, 400.0, 1200.0, 3500.0, 8000.0]
+    out["held_out_re"] = held_out
+    for n, cap in ((256, args.learned_cap * 2), (1024, args.learned_cap_1024)):
+        cold, fc = WS.time_to_steady(held_out, n, None, args.tol, 1000, cap)
+        warm, fw = WS.time_to_steady(held_out, n, net, args.tol, 1000, cap)
+        diff = [float((a - b).abs().max().item() / WS.U_LID) for a, b in zip(fc, fw)]
+        both = [k for k in range(len(held_out)) if cold["state"][k] == 1 and warm["state"][k] == 1]
+        factors = [cold["steps"][k] / warm["steps"][k] for k in both]
+        out["n%d" % n] = {"cold": cold, "warm": warm, "final_field_max_diff_over_U": diff,
+                          "steps_factor_converged": factors,
+                          "steps_factor_geomean": float(np.exp(np.mean(np.log(factors)))) if factors else None,
+                          "wall_factor": cold["wall_s"] / warm["wall_s"]}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def _oracle_cavity_u(n, re, steps):
     """FP64 oracle: u after `steps` updates of an n x n cavity (U_lid = 0.1) at Reynolds number re."""
     import oracle as O
@@ -578,6 +621,8 @@ def main(argv=None):
         return precision_report(args)
     if args.report == "batched":
         return batched_report(args)
+    if args.report == "learned":
+        return learned_report(args)
     if args.report == "batched-throughput":
         import torch
         import paper_2409_01076_gb300 as S

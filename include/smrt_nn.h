@@ -1,0 +1,91 @@
+/*
+ * smrt_nn.h -- C ABI of the small neural-network kernel set used by the learned
+ * warm start: a U-Net that predicts a steady cavity field (u, v, rho) from the
+ * Reynolds number and the node coordinates, after which the SmrtLBM update of
+ * smrt.h iterates to the steady-state tolerance.  The paper has no network;
+ * this is the library's own addition, built on the same CUDA library.
+ *
+ * Conventions
+ * - Every pointer is DEVICE memory of the current device; every call enqueues
+ *   work on `stream` (a cudaStream_t, NULL = legacy default stream) and returns
+ *   SMRT_OK or SMRT_ERR_ARG / SMRT_ERR_CUDA (message in smrt_last_error(NULL)).
+ *   Nothing is allocated and nothing is freed.
+ * - Activations are float32 NHWC: x[n][y][x][c], row-major, dense.
+ * - Matrix operands of smrt_nn_gemm are IEEE half; accumulation is float32.
+ */
+#ifndef SMRT_NN_H
+#define SMRT_NN_H
+
+#include "smrt.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* C = alpha * op(A) * op(B) + beta * C, op(A) M x K, op(B) K x N, C M x N float32
+ * row-major with leading dimension ldc.  A (half, leading dimension lda) holds
+ * op(A) row-major when transA == 0 and op(A)^T (K x M) row-major when transA == 1;
+ * B (half, ldb) holds op(B) (K x N) when transB == 0 and op(B)^T (N x K) when 1.
+ * split_k > 1 splits the K range over split_k blocks that ATOMICALLY ADD their
+ * partial products into C (C must hold the beta * C part already; beta is then
+ * ignored).  Tensor-core (WMMA 16x16x16) tiles of 64 x 64 x 32. */
+SMRT_API int smrt_nn_gemm(int transA, int transB, int M, int N, int K, float alpha, const void *A, int lda,
+                          const void *B, int ldb, float beta, float *C, int ldc, int split_k, void *stream);
+
+/* 3x3, stride 1, zero padding 1 patches of x (N,H,W,C float32) into
+ * col (N*H*W rows x 9*C half, row-major): col[p][(ky*3+kx)*C + c] = x[n][y+ky-1][x+kx-1][c]. */
+SMRT_API int smrt_nn_im2col3(const float *x, int N, int H, int W, int C, void *col, void *stream);
+
+/* Adjoint of smrt_nn_im2col3: dx[n][y][x][c] = sum over the 9 patches that read it of dcol (float32). */
+SMRT_API int smrt_nn_col2im3(const float *dcol, int N, int H, int W, int C, float *dx, void *stream);
+
+/* dst[i] = (half)(scale * src[i]), n elements. */
+SMRT_API int smrt_nn_to_half(const float *src, long long n, float scale, void *dst, void *stream);
+
+/* z = x + bias[c] (x, z: rows x C), then a = SiLU(z) = z / (1 + exp(-z)) if act, else a = z.
+ * z may be NULL (not kept); a may alias x. */
+SMRT_API int smrt_nn_bias_act(const float *x, const float *bias, long long rows, int C, int act, float *z, float *a,
+                              void *stream);
+
+/* Backward of smrt_nn_bias_act: dz = da * SiLU'(z) (or da), db[c] += sum over rows of dz.
+ * dz may alias da; db is accumulated into (zero it first). */
+SMRT_API int smrt_nn_bias_act_bwd(const float *da, const float *z, long long rows, int C, int act, float *dz,
+                                  float *db, void *stream);
+
+/* 2x2 average pooling (H, W even) and its adjoint. */
+SMRT_API int smrt_nn_avgpool2(const float *x, int N, int H, int W, int C, float *y, void *stream);
+SMRT_API int smrt_nn_avgpool2_bwd(const float *dy, int N, int H, int W, int C, float *dx, void *stream);
+
+/* Nearest-neighbour 2x upsampling of (N,H,W,C) to (N,2H,2W,C) and its adjoint. */
+SMRT_API int smrt_nn_upsample2(const float *x, int N, int H, int W, int C, float *y, void *stream);
+SMRT_API int smrt_nn_upsample2_bwd(const float *dy, int N, int H, int W, int C, float *dx, void *stream);
+
+/* Channel concatenation y = [a | b] of (rows, Ca) and (rows, Cb), and its adjoint
+ * (da, db may be NULL to skip). */
+SMRT_API int smrt_nn_concat(const float *a, int Ca, const float *b, int Cb, long long rows, float *y, void *stream);
+SMRT_API int smrt_nn_concat_bwd(const float *dy, int Ca, int Cb, long long rows, float *da, float *db, void *stream);
+
+/* y = a + b, n elements (y may alias a or b). */
+SMRT_API int smrt_nn_add(const float *a, const float *b, long long n, float *y, void *stream);
+
+/* Mean squared error L = mean((y - t)^2) over n elements: loss[0] += L (double,
+ * zero it first); dy = grad_scale * 2 (y - t) / n (dy may be NULL). */
+SMRT_API int smrt_nn_mse(const float *y, const float *t, long long n, float grad_scale, double *loss, float *dy,
+                         void *stream);
+
+/* Adam step on n parameters: g = grad / grad_scale, m = b1 m + (1 - b1) g,
+ * v = b2 v + (1 - b2) g^2, w -= lr * (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
+ * Non-finite gradients leave w, m, v unchanged and set found_inf[0] = 1. */
+SMRT_API int smrt_nn_adam(float *w, const float *grad, float *m, float *v, long long n, float lr, float b1, float b2,
+                          float eps, int step, float grad_scale, int *found_inf, void *stream);
+
+/* Bilinear resampling of (N,H,W,C) to (N,H2,W2,C), node-centred on the unit square:
+ * output node (i, j) samples the input at ((i + 1/2) H / H2 - 1/2, ...), clamped at the edges. */
+SMRT_API int smrt_nn_resize_bilinear(const float *x, int N, int H, int W, int C, float *y, int H2, int W2,
+                                     void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SMRT_NN_H */

@@ -50,6 +50,25 @@ SIGNATURES = [
     ("smrt_batch_nodes", c_longlong, [c_void_p]),
     ("smrt_batch_last_error", c_char_p, [c_void_p]),
     ("smrt_batch_destroy", None, [c_void_p]),
+    # include/smrt_nn.h
+    ("smrt_nn_gemm", c_int, [c_int, c_int, c_int, c_int, c_int, ctypes.c_float, c_void_p, c_int, c_void_p, c_int,
+                             ctypes.c_float, c_void_p, c_int, c_int, c_void_p]),
+    ("smrt_nn_im2col3", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p]),
+    ("smrt_nn_col2im3", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p]),
+    ("smrt_nn_to_half", c_int, [c_void_p, c_longlong, ctypes.c_float, c_void_p, c_void_p]),
+    ("smrt_nn_bias_act", c_int, [c_void_p, c_void_p, c_longlong, c_int, c_int, c_void_p, c_void_p, c_void_p]),
+    ("smrt_nn_bias_act_bwd", c_int, [c_void_p, c_void_p, c_longlong, c_int, c_int, c_void_p, c_void_p, c_void_p]),
+    ("smrt_nn_avgpool2", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p]),
+    ("smrt_nn_avgpool2_bwd", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p]),
+    ("smrt_nn_upsample2", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p]),
+    ("smrt_nn_upsample2_bwd", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p]),
+    ("smrt_nn_concat", c_int, [c_void_p, c_int, c_void_p, c_int, c_longlong, c_void_p, c_void_p]),
+    ("smrt_nn_concat_bwd", c_int, [c_void_p, c_int, c_int, c_longlong, c_void_p, c_void_p, c_void_p]),
+    ("smrt_nn_add", c_int, [c_void_p, c_void_p, c_longlong, c_void_p, c_void_p]),
+    ("smrt_nn_mse", c_int, [c_void_p, c_void_p, c_longlong, ctypes.c_float, c_void_p, c_void_p, c_void_p]),
+    ("smrt_nn_adam", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_longlong, ctypes.c_float, ctypes.c_float,
+                             ctypes.c_float, ctypes.c_float, c_int, ctypes.c_float, c_void_p, c_void_p]),
+    ("smrt_nn_resize_bilinear", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_int, c_int, c_void_p]),
 ]
 
 

@@ -1,0 +1,103 @@
+"""Bindings of include/smrt_nn.h (same names; argument marshalling only).
+
+Tensors are CUDA torch tensors on the current device; every call runs on the
+current torch stream.  A non-OK status raises SmrtError.
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import _lib
+
+
+def _p(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _s():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _check(rc):
+    if rc != 0:
+        from . import SmrtError, smrt_last_error
+        raise SmrtError(rc, smrt_last_error(None))
+
+
+def smrt_nn_gemm(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, split_k=1):
+    _check(_lib.load().smrt_nn_gemm(int(transA), int(transB), int(M), int(N), int(K), float(alpha), _p(A), int(lda),
+                                    _p(B), int(ldb), float(beta), _p(C), int(ldc), int(split_k), _s()))
+
+
+def smrt_nn_im2col3(x, col):
+    n, h, w, c = x.shape
+    _check(_lib.load().smrt_nn_im2col3(_p(x), n, h, w, c, _p(col), _s()))
+
+
+def smrt_nn_col2im3(dcol, shape, dx):
+    n, h, w, c = shape
+    _check(_lib.load().smrt_nn_col2im3(_p(dcol), n, h, w, c, _p(dx), _s()))
+
+
+def smrt_nn_to_half(src, dst, scale=1.0):
+    _check(_lib.load().smrt_nn_to_half(_p(src), src.numel(), float(scale), _p(dst), _s()))
+
+
+def smrt_nn_bias_act(x, bias, act, z, a):
+    rows = x.numel() // x.shape[-1]
+    _check(_lib.load().smrt_nn_bias_act(_p(x), _p(bias), rows, x.shape[-1], int(act), _p(z), _p(a), _s()))
+
+
+def smrt_nn_bias_act_bwd(da, z, act, dz, db):
+    rows = da.numel() // da.shape[-1]
+    _check(_lib.load().smrt_nn_bias_act_bwd(_p(da), _p(z), rows, da.shape[-1], int(act), _p(dz), _p(db), _s()))
+
+
+def smrt_nn_avgpool2(x, y):
+    n, h, w, c = x.shape
+    _check(_lib.load().smrt_nn_avgpool2(_p(x), n, h, w, c, _p(y), _s()))
+
+
+def smrt_nn_avgpool2_bwd(dy, shape, dx):
+    n, h, w, c = shape
+    _check(_lib.load().smrt_nn_avgpool2_bwd(_p(dy), n, h, w, c, _p(dx), _s()))
+
+
+def smrt_nn_upsample2(x, y):
+    n, h, w, c = x.shape
+    _check(_lib.load().smrt_nn_upsample2(_p(x), n, h, w, c, _p(y), _s()))
+
+
+def smrt_nn_upsample2_bwd(dy, shape, dx):
+    n, h, w, c = shape
+    _check(_lib.load().smrt_nn_upsample2_bwd(_p(dy), n, h, w, c, _p(dx), _s()))
+
+
+def smrt_nn_concat(a, b, y):
+    rows = a.numel() // a.shape[-1]
+    _check(_lib.load().smrt_nn_concat(_p(a), a.shape[-1], _p(b), b.shape[-1], rows, _p(y), _s()))
+
+
+def smrt_nn_concat_bwd(dy, ca, cb, da, db):
+    rows = dy.numel() // dy.shape[-1]
+    _check(_lib.load().smrt_nn_concat_bwd(_p(dy), int(ca), int(cb), rows, _p(da), _p(db), _s()))
+
+
+def smrt_nn_add(a, b, y):
+    _check(_lib.load().smrt_nn_add(_p(a), _p(b), a.numel(), _p(y), _s()))
+
+
+def smrt_nn_mse(y, t, grad_scale, loss, dy):
+    _check(_lib.load().smrt_nn_mse(_p(y), _p(t), y.numel(), float(grad_scale), _p(loss), _p(dy), _s()))
+
+
+def smrt_nn_adam(w, grad, m, v, lr, b1, b2, eps, step, grad_scale, found_inf):
+    _check(_lib.load().smrt_nn_adam(_p(w), _p(grad), _p(m), _p(v), w.numel(), float(lr), float(b1), float(b2),
+                                    float(eps), int(step), float(grad_scale), _p(found_inf), _s()))
+
+
+def smrt_nn_resize_bilinear(x, y):
+    n, h, w, c = x.shape
+    _, h2, w2, _ = y.shape
+    _check(_lib.load().smrt_nn_resize_bilinear(_p(x), n, h, w, c, _p(y), h2, w2, _s()))

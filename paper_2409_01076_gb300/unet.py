@@ -1,0 +1,254 @@
+"""U-Net of the learned warm start, trained and run on the GPU by libsmrt's NN kernels.
+
+The network maps three input channels -- the normalised Reynolds number and the
+two node coordinates -- to three output channels (u / U, v / U, (rho - 1) / (3 U^2))
+of a steady lid-driven cavity.  Every arithmetic step runs in the kernels of
+include/smrt_nn.h; PyTorch only allocates the tensors and supplies the stream.
+
+Architecture (4 levels, `base` channels at the top; 32 in use):
+    enc1: conv3(3 -> b), conv3(b -> b)                  (H)
+    enc2: pool, conv3(b -> 2b), conv3(2b -> 2b)         (H/2)
+    enc3: pool, conv3(2b -> 4b), conv3(4b -> 4b)        (H/4)
+    mid : pool, conv3(4b -> 8b), conv3(8b -> 8b)        (H/8)
+    dec3: up, [. | enc3], conv3(12b -> 4b), conv3(4b -> 4b)
+    dec2: up, [. | enc2], conv3(6b -> 2b), conv3(2b -> 2b)
+    dec1: up, [. | enc1], conv3(3b -> b), conv3(b -> b)
+    head: conv1(b -> 3), linear
+3x3 convolutions pad with zeros; activations are SiLU; pooling is 2x2 average;
+upsampling is nearest.  A 3x3 weight is stored (cout, 9 cin) with column
+(ky * 3 + kx) * cin + c.  Matrix products take half operands with float32
+accumulation; master weights, gradients and optimiser state are float32.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import nn as K
+
+LAYERS = [  # name, cin multiple of b (or the input), cout multiple of b, kernel, activation
+    ("enc1a", "in", 1, 3, True), ("enc1b", 1, 1, 3, True),
+    ("enc2a", 1, 2, 3, True), ("enc2b", 2, 2, 3, True),
+    ("enc3a", 2, 4, 3, True), ("enc3b", 4, 4, 3, True),
+    ("mida", 4, 8, 3, True), ("midb", 8, 8, 3, True),
+    ("dec3a", 12, 4, 3, True), ("dec3b", 4, 4, 3, True),
+    ("dec2a", 6, 2, 3, True), ("dec2b", 2, 2, 3, True),
+    ("dec1a", 3, 1, 3, True), ("dec1b", 1, 1, 3, True),
+    ("head", 1, "out", 1, False),
+]
+
+RE_LO, RE_HI = 100.0, 10000.0
+
+
+def re_feature(re: float) -> float:
+    """log(Re) mapped linearly so that Re = 100 -> 0 and Re = 10^4 -> 1."""
+    return (math.log(re) - math.log(RE_LO)) / (math.log(RE_HI) - math.log(RE_LO))
+
+
+class UNet:
+    def __init__(self, base: int = 32, cin: int = 3, cout: int = 3, seed: int = 0, device: str = "cuda"):
+        import torch
+        self.torch = torch
+        self.base, self.cin, self.cout, self.device = base, cin, cout, device
+        self.specs = []
+        for name, ci, co, k, act in LAYERS:
+            ci = cin if ci == "in" else ci * base
+            co = cout if co == "out" else co * base
+            self.specs.append((name, ci, co, k, act))
+        rng = np.random.Generator(np.random.PCG64(seed))
+        self.params, self.grads, self.m, self.v = {}, {}, {}, {}
+        for name, ci, co, k, _ in self.specs:
+            fan_in = ci * k * k
+            w = rng.normal(0.0, math.sqrt(2.0 / fan_in), size=(co, k * k * ci))
+            b = rng.normal(0.0, 0.01, size=(co,))
+            for key, val in ((name + ".w", w), (name + ".b", b)):
+                self.params[key] = torch.tensor(val, dtype=torch.float32, device=device)
+                self.grads[key] = torch.zeros_like(self.params[key])
+                self.m[key] = torch.zeros_like(self.params[key])
+                self.v[key] = torch.zeros_like(self.params[key])
+        self.step_count = 0
+        self.grad_scale = 2.0 ** 16
+        self._found_inf = torch.zeros(1, dtype=torch.int32, device=device)
+        self._loss = torch.zeros(1, dtype=torch.float64, device=device)
+
+    # ---- parameters --------------------------------------------------------------------
+    def load_numpy(self, params: dict) -> None:
+        for key, val in params.items():
+            self.params[key].copy_(self.torch.tensor(val, dtype=self.torch.float32))
+
+    def to_numpy(self) -> dict:
+        return {k: v.detach().cpu().numpy().astype(np.float64) for k, v in self.params.items()}
+
+    def n_params(self) -> int:
+        return sum(p.numel() for p in self.params.values())
+
+    # ---- one convolution (3x3 via im2col, or 1x1) ----------------------------------------
+    def _half_weights(self):
+        t = self.torch
+        self._wh = {}
+        for name, ci, co, k, _ in self.specs:
+            w = self.params[name + ".w"]
+            h = t.empty(w.shape, dtype=t.float16, device=self.device)
+            K.smrt_nn_to_half(w, h)
+            self._wh[name] = h
+
+    def _conv(self, spec, x, cache):
+        t = self.torch
+        name, ci, co, k, act = spec
+        n, h, w, _ = x.shape
+        rows = n * h * w
+        kk = k * k * ci
+        col = t.empty((rows, kk), dtype=t.float16, device=self.device)
+        if k == 3:
+            K.smrt_nn_im2col3(x, col)
+        else:
+            K.smrt_nn_to_half(x, col)
+        y = t.empty((n, h, w, co), dtype=t.float32, device=self.device)
+        K.smrt_nn_gemm(0, 1, rows, co, kk, 1.0, col, kk, self._wh[name], kk, 0.0, y, co)
+        z = t.empty_like(y) if (act and cache is not None) else None
+        K.smrt_nn_bias_act(y, self.params[name + ".b"], act, z, y)
+        if cache is not None:
+            cache[name] = (col, z, x.shape)
+        return y
+
+    def _conv_bwd(self, spec, da, cache, need_dx=True):
+        t = self.torch
+        name, ci, co, k, act = spec
+        col, z, xshape = cache[name]
+        n, h, w, _ = xshape
+        rows = n * h * w
+        kk = k * k * ci
+        dz = t.empty_like(da)
+        K.smrt_nn_bias_act_bwd(da, z, act, dz, self.grads[name + ".b"])
+        dzh = t.empty(dz.shape, dtype=t.float16, device=self.device)
+        K.smrt_nn_to_half(dz, dzh)
+        split = max(1, min(256, rows // 8192))
+        K.smrt_nn_gemm(1, 0, co, kk, rows, 1.0, dzh, co, col, kk, 1.0, self.grads[name + ".w"], kk, split)
+        if not need_dx:
+            return None
+        dcol = t.empty((rows, kk), dtype=t.float32, device=self.device)
+        K.smrt_nn_gemm(0, 0, rows, kk, co, 1.0, dzh, co, self._wh[name], kk, 0.0, dcol, kk)
+        if k == 1:
+            return dcol.view(xshape)
+        dx = t.empty(xshape, dtype=t.float32, device=self.device)
+        K.smrt_nn_col2im3(dcol, xshape, dx)
+        return dx
+
+    # ---- the network ------------------------------------------------------------------
+    def _pool(self, x):
+        n, h, w, c = x.shape
+        y = self.torch.empty((n, h // 2, w // 2, c), dtype=self.torch.float32, device=self.device)
+        K.smrt_nn_avgpool2(x, y)
+        return y
+
+    def _up(self, x):
+        n, h, w, c = x.shape
+        y = self.torch.empty((n, 2 * h, 2 * w, c), dtype=self.torch.float32, device=self.device)
+        K.smrt_nn_upsample2(x, y)
+        return y
+
+    def _cat(self, a, b):
+        n, h, w, ca = a.shape
+        y = self.torch.empty((n, h, w, ca + b.shape[3]), dtype=self.torch.float32, device=self.device)
+        K.smrt_nn_concat(a, b, y)
+        return y
+
+    def forward(self, x, cache=None):
+        """x: (N, H, W, cin) float32 CUDA, H and W divisible by 8.  Returns (N, H, W, cout)."""
+        s = {sp[0]: sp for sp in self.specs}
+        self._half_weights()
+        c = lambda name, inp: self._conv(s[name], inp, cache)  # noqa: E731
+        e1 = c("enc1b", c("enc1a", x))
+        e2 = c("enc2b", c("enc2a", self._pool(e1)))
+        e3 = c("enc3b", c("enc3a", self._pool(e2)))
+        m = c("midb", c("mida", self._pool(e3)))
+        d3 = c("dec3b", c("dec3a", self._cat(self._up(m), e3)))
+        d2 = c("dec2b", c("dec2a", self._cat(self._up(d3), e2)))
+        d1 = c("dec1b", c("dec1a", self._cat(self._up(d2), e1)))
+        return c("head", d1)
+
+    def backward(self, dy, cache):
+        """Accumulates scaled gradients of the loss into self.grads from dL/dy (already scaled)."""
+        t = self.torch
+        s = {sp[0]: sp for sp in self.specs}
+        b = self.base
+        cb = lambda name, da, need=True: self._conv_bwd(s[name], da, cache, need)  # noqa: E731
+
+        def split(dcat, ca):
+            n, h, w, cc = dcat.shape
+            da = t.empty((n, h, w, ca), dtype=t.float32, device=self.device)
+            db = t.empty((n, h, w, cc - ca), dtype=t.float32, device=self.device)
+            K.smrt_nn_concat_bwd(dcat, ca, cc - ca, da, db)
+            return da, db
+
+        def up_bwd(dyy):
+            n, h, w, cc = dyy.shape
+            dx = t.empty((n, h // 2, w // 2, cc), dtype=t.float32, device=self.device)
+            K.smrt_nn_upsample2_bwd(dyy, (n, h // 2, w // 2, cc), dx)
+            return dx
+
+        def pool_bwd(dyy):
+            n, h, w, cc = dyy.shape
+            dx = t.empty((n, 2 * h, 2 * w, cc), dtype=t.float32, device=self.device)
+            K.smrt_nn_avgpool2_bwd(dyy, (n, 2 * h, 2 * w, cc), dx)
+            return dx
+
+        def add_into(acc, other):        # acc += other (skip path + pooled path)
+            K.smrt_nn_add(acc, other, acc)
+            return acc
+
+        dd1 = cb("head", dy)
+        du2, de1 = split(cb("dec1a", cb("dec1b", dd1)), 2 * b)
+        du3, de2 = split(cb("dec2a", cb("dec2b", up_bwd(du2))), 4 * b)
+        dum, de3 = split(cb("dec3a", cb("dec3b", up_bwd(du3))), 8 * b)
+        de3 = add_into(de3, pool_bwd(cb("mida", cb("midb", up_bwd(dum)))))
+        de2 = add_into(de2, pool_bwd(cb("enc3a", cb("enc3b", de3))))
+        de1 = add_into(de1, pool_bwd(cb("enc2a", cb("enc2b", de2))))
+        cb("enc1a", cb("enc1b", de1), need=False)
+
+    def loss_and_grad(self, x, target):
+        """MSE loss (float) with scaled gradients accumulated into self.grads (zeroed first)."""
+        for g in self.grads.values():
+            g.zero_()
+        cache = {}
+        y = self.forward(x, cache)
+        self._loss.zero_()
+        dy = self.torch.empty_like(y)
+        K.smrt_nn_mse(y, target, self.grad_scale, self._loss, dy)
+        self.backward(dy, cache)
+        return y
+
+    def adam_step(self, lr: float, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8) -> bool:
+        """Applies the accumulated gradients; returns False (and lowers the loss scale) on overflow."""
+        self.step_count += 1
+        self._found_inf.zero_()
+        for key in self.params:
+            K.smrt_nn_adam(self.params[key], self.grads[key], self.m[key], self.v[key], lr, b1, b2, eps,
+                           self.step_count, self.grad_scale, self._found_inf)
+        if int(self._found_inf.item()):
+            self.grad_scale /= 2.0
+            return False
+        return True
+
+    def train_step(self, x, target, lr: float) -> float:
+        self.loss_and_grad(x, target)
+        self.adam_step(lr)
+        return float(self._loss.item())
+
+    def predict(self, x):
+        return self.forward(x, None)
+
+
+def input_grid(res, h: int, w: int, device: str = "cuda"):
+    """Network input (len(res), h, w, 3): [re_feature, x, y] with node-centred x = (i + 1/2) / w."""
+    import torch
+    n = len(res)
+    x = torch.empty((n, h, w, 3), dtype=torch.float32, device=device)
+    xs = (torch.arange(w, dtype=torch.float32, device=device) + 0.5) / w
+    ys = (torch.arange(h, dtype=torch.float32, device=device) + 0.5) / h
+    x[..., 1] = xs.view(1, 1, w)
+    x[..., 2] = ys.view(1, h, 1)
+    for k, re in enumerate(res):
+        x[k, ..., 0] = re_feature(re)
+    return x

@@ -1,0 +1,191 @@
+"""NN kernels of the learned warm start against numpy, and the GPU U-Net's loss
+and gradients against the FP64 oracle (oracle/unet_oracle.py) with the same weights."""
+import numpy as np
+import pytest
+
+import paper_2409_01076_gb300 as S
+from oracle import unet_oracle as U
+
+pytestmark = pytest.mark.gpu
+
+
+def _t(a, dtype=None):
+    import torch
+    return torch.tensor(np.asarray(a), dtype=dtype or torch.float32, device="cuda")
+
+
+def _np(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.detach().cpu().double().numpy()
+
+
+def _rng(s):
+    return np.random.Generator(np.random.PCG64(s))
+
+
+@pytest.mark.parametrize("transA", [0, 1])
+@pytest.mark.parametrize("transB", [0, 1])
+@pytest.mark.parametrize("split", [1, 3])
+def test_gemm_all_layouts(transA, transB, split):
+    import torch
+    r = _rng(transA * 4 + transB * 2 + split)
+    M, N, Kd = 70, 45, 137
+    a = r.normal(size=(Kd, M) if transA else (M, Kd)).astype(np.float16)
+    b = r.normal(size=(N, Kd) if transB else (Kd, N)).astype(np.float16)
+    c0 = r.normal(size=(M, N)).astype(np.float32)
+    A = _t(a, torch.float16)
+    B = _t(b, torch.float16)
+    C = _t(c0)
+    opa = a.astype(np.float64).T if transA else a.astype(np.float64)
+    opb = b.astype(np.float64).T if transB else b.astype(np.float64)
+    if split == 1:
+        S.smrt_nn_gemm(transA, transB, M, N, Kd, 0.5, A, a.shape[1], B, b.shape[1], 2.0, C, N, 1)
+        ref = 0.5 * opa @ opb + 2.0 * c0
+    else:
+        S.smrt_nn_gemm(transA, transB, M, N, Kd, 0.5, A, a.shape[1], B, b.shape[1], 1.0, C, N, split)
+        ref = 0.5 * opa @ opb + c0           # split-K accumulates into C
+    assert np.abs(_np(C) - ref).max() <= 1e-4 * np.abs(ref).max()
+
+
+def test_im2col_col2im_match_oracle():
+    import torch
+    r = _rng(3)
+    x = r.normal(size=(2, 6, 10, 5))
+    col = torch.empty((2 * 6 * 10, 45), dtype=torch.float16, device="cuda")
+    S.smrt_nn_im2col3(_t(x), col)
+    assert np.abs(_np(col) - U.im2col3(x.astype(np.float32).astype(np.float16).astype(np.float64))).max() == 0
+    d = r.normal(size=(2 * 6 * 10, 45))
+    dx = torch.empty((2, 6, 10, 5), dtype=torch.float32, device="cuda")
+    S.smrt_nn_col2im3(_t(d), (2, 6, 10, 5), dx)
+    assert np.abs(_np(dx) - U.col2im3(d, (2, 6, 10, 5))).max() < 1e-5
+
+
+def test_bias_act_forward_backward():
+    import torch
+    r = _rng(4)
+    x = r.normal(size=(300, 7)) * 3
+    b = r.normal(size=(7,))
+    z = torch.empty((300, 7), device="cuda")
+    a = torch.empty((300, 7), device="cuda")
+    S.smrt_nn_bias_act(_t(x), _t(b), 1, z, a)
+    zr = x + b
+    assert np.abs(_np(z) - zr).max() < 1e-5
+    assert np.abs(_np(a) - U.silu(zr)).max() < 1e-5
+    da = r.normal(size=(300, 7))
+    dz = torch.empty((300, 7), device="cuda")
+    db = torch.zeros(7, device="cuda")
+    S.smrt_nn_bias_act_bwd(_t(da), z, 1, dz, db)
+    dzr = da * U.silu_grad(zr)
+    assert np.abs(_np(dz) - dzr).max() < 1e-5
+    assert np.abs(_np(db) - dzr.sum(axis=0)).max() < 1e-4
+
+
+def test_pool_upsample_concat_add():
+    import torch
+    r = _rng(5)
+    x = r.normal(size=(2, 8, 6, 3))
+    y = torch.empty((2, 4, 3, 3), device="cuda")
+    S.smrt_nn_avgpool2(_t(x), y)
+    assert np.abs(_np(y) - U.pool(x)).max() < 1e-6
+    dx = torch.empty((2, 8, 6, 3), device="cuda")
+    S.smrt_nn_avgpool2_bwd(y, (2, 8, 6, 3), dx)
+    assert np.abs(_np(dx) - U.pool_bwd(_np(y))).max() < 1e-6
+    u = torch.empty((2, 16, 12, 3), device="cuda")
+    S.smrt_nn_upsample2(_t(x), u)
+    assert np.abs(_np(u) - U.up(x)).max() < 1e-6
+    S.smrt_nn_upsample2_bwd(u, (2, 8, 6, 3), dx)
+    assert np.abs(_np(dx) - U.up_bwd(_np(u))).max() < 1e-5
+    a2 = r.normal(size=(2, 8, 6, 2))
+    cat = torch.empty((2, 8, 6, 5), device="cuda")
+    S.smrt_nn_concat(_t(x), _t(a2), cat)
+    assert np.abs(_np(cat) - np.concatenate([x, a2], axis=3)).max() < 1e-6
+    da = torch.empty((2, 8, 6, 3), device="cuda")
+    db = torch.empty((2, 8, 6, 2), device="cuda")
+    S.smrt_nn_concat_bwd(cat, 3, 2, da, db)
+    assert np.abs(_np(da) - x).max() < 1e-6 and np.abs(_np(db) - a2).max() < 1e-6
+    s = torch.empty((2, 8, 6, 3), device="cuda")
+    S.smrt_nn_add(_t(x), _t(x), s)
+    assert np.abs(_np(s) - 2 * x).max() < 1e-5
+
+
+def test_mse_and_adam():
+    import torch
+    r = _rng(6)
+    y, t = r.normal(size=1000), r.normal(size=1000)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    dy = torch.empty(1000, device="cuda")
+    S.smrt_nn_mse(_t(y), _t(t), 8.0, loss, dy)
+    ya, ta = y.astype(np.float32).astype(np.float64), t.astype(np.float32).astype(np.float64)
+    assert abs(_np(loss)[0] - np.mean((ya - ta) ** 2)) < 1e-9
+    assert np.abs(_np(dy) - 8.0 * 2 * (ya - ta) / 1000).max() < 1e-6
+    w0, g = r.normal(size=50), r.normal(size=50)
+    w, m, v = _t(w0), torch.zeros(50, device="cuda"), torch.zeros(50, device="cuda")
+    inf = torch.zeros(1, dtype=torch.int32, device="cuda")
+    wr, mr, vr = w0.copy(), np.zeros(50), np.zeros(50)
+    for step in (1, 2, 3):
+        S.smrt_nn_adam(w, _t(4.0 * g), m, v, 1e-2, 0.9, 0.999, 1e-8, step, 4.0, inf)
+        mr = 0.9 * mr + 0.1 * g
+        vr = 0.999 * vr + 0.001 * g * g
+        wr = wr - 1e-2 * (mr / (1 - 0.9 ** step)) / (np.sqrt(vr / (1 - 0.999 ** step)) + 1e-8)
+    assert np.abs(_np(w) - wr).max() < 1e-5 and int(_np(inf)[0]) == 0
+    bad = g.copy()
+    bad[3] = np.inf
+    S.smrt_nn_adam(w, _t(bad), m, v, 1e-2, 0.9, 0.999, 1e-8, 4, 1.0, inf)
+    assert int(_np(inf)[0]) == 1
+
+
+def test_resize_bilinear_special_cases():
+    import torch
+    r = _rng(7)
+    x = r.normal(size=(1, 8, 8, 2))
+    y = torch.empty((1, 8, 8, 2), device="cuda")
+    S.smrt_nn_resize_bilinear(_t(x), y)
+    assert np.abs(_np(y) - x).max() < 1e-6                       # same size: identity
+    # a field linear in the node coordinates is reproduced exactly away from the clamped edges
+    h, h2 = 16, 64
+    yy, xx = np.meshgrid((np.arange(h) + 0.5) / h, (np.arange(h) + 0.5) / h, indexing="ij")
+    lin = np.stack([2 * xx - yy, 0.5 + yy], axis=-1)[None]
+    out = torch.empty((1, h2, h2, 2), device="cuda")
+    S.smrt_nn_resize_bilinear(_t(lin), out)
+    y2, x2 = np.meshgrid((np.arange(h2) + 0.5) / h2, (np.arange(h2) + 0.5) / h2, indexing="ij")
+    ref = np.stack([2 * x2 - y2, 0.5 + y2], axis=-1)[None]
+    inner = slice(4, h2 - 4)
+    assert np.abs(_np(out)[:, inner, inner] - ref[:, inner, inner]).max() < 1e-5
+
+
+def test_unet_loss_and_gradients_match_oracle():
+    """Same weights, same batch: loss and every gradient tensor within half-precision operand rounding."""
+    from paper_2409_01076_gb300.unet import UNet
+    base, n, h, w = 8, 2, 16, 16
+    params = U.init_params(base, seed=3)
+    r = _rng(8)
+    x = r.uniform(0, 1, size=(n, h, w, 3))
+    t = 0.3 * r.normal(size=(n, h, w, 3))
+    loss_ref, grads_ref, _ = U.loss_and_grads(params, x, t, base)
+    net = UNet(base=base)
+    net.load_numpy(params)
+    net.grad_scale = 1024.0
+    net.loss_and_grad(_t(x), _t(t))
+    loss = float(_np(net._loss)[0])
+    assert abs(loss / loss_ref - 1) < 5e-3, (loss, loss_ref)
+    for key, gr in grads_ref.items():
+        g = _np(net.grads[key]) / net.grad_scale
+        rel = np.linalg.norm(g - gr) / max(np.linalg.norm(gr), 1e-30)
+        cos = (g * gr).sum() / max(np.linalg.norm(g) * np.linalg.norm(gr), 1e-30)
+        assert rel < 3e-2 and cos > 0.999, (key, rel, cos)
+
+
+def test_unet_training_reduces_the_loss():
+    from paper_2409_01076_gb300.unet import UNet, input_grid
+    net = UNet(base=8, seed=1)
+    x = input_grid([150.0, 900.0], 32, 32)
+    r = _rng(9)
+    # a smooth synthetic target: a function of the inputs the network must learn
+    xs = _np(x)
+    t = np.stack([np.sin(3 * xs[..., 1]) * xs[..., 0], np.cos(2 * xs[..., 2]), xs[..., 1] * xs[..., 2]], axis=-1)
+    tt = _t(t)
+    first = net.train_step(x, tt, 3e-3)
+    for _ in range(150):
+        last = net.train_step(x, tt, 3e-3)
+    assert last < 0.2 * first, (first, last)
