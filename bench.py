@@ -48,7 +48,7 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--size", type=int, default=0,
                    help="override the lattice side (profiling on a smaller case of the same workload)")
-    p.add_argument("--report", choices=["", "precision", "batched", "batched-throughput", "learned"], default="",
+    p.add_argument("--report", choices=["", "precision", "batched", "batched-throughput", "learned", "paper"], default="",
                    help="precision: 16-bit vs FP32 storage report; batched: 512 cavities to steady state "
                         "(each prints its own JSON line)")
     p.add_argument("--learned-count", type=int, default=2000)
@@ -502,6 +502,65 @@ def batched_report(args):
     return 0
 
 
+def paper_experiments_report(args):
+    """The paper's cavity experiments as stability demonstrations, SmrtLBM against SRT on the same GPU.
+
+    Lattice parameters follow the paper's statement (tau fixed, Re = U L / nu with L = n under halfway
+    bounce-back, nu = (tau - 1/2) / 3), so U_lid = Re nu / n:
+      E1: 100^2, Re 1,000, tau 0.51, 60,000 steps (steady state claimed);
+      E2: Re 10,000, tau 0.51 on 100^2, 200^2, 250^2;
+      E4: 400^2, Re 100,000, tau 0.502, 100,000 steps (no instability claimed).
+    Reports divergence (the flag), steps completed and the final one-step and stride residuals."""
+    import numpy as np
+    import torch
+    import paper_2409_01076_gb300 as S
+    from paper_2409_01076_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    S._lib.load()
+    cases = [("E1", 100, 1000.0, 0.51, 60000), ("E2", 100, 1e4, 0.51, 60000), ("E2", 200, 1e4, 0.51, 60000),
+             ("E2", 250, 1e4, 0.51, 100000), ("E4", 400, 1e5, 0.502, 100000)]
+    out = {"report": "paper-experiments", "cases": []}
+    for name, n, re, tau, steps in cases:
+        nu = (tau - 0.5) / 3.0
+        u_lid = re * nu / n
+        for kind, kname in ((S.SMRT_COLLISION_SMRT, "smrt"), (S.SMRT_COLLISION_SRT, "srt")):
+            h = S.smrt_create(n, n, tau, u_lid, W.CAVITY)
+            S.smrt_set_option(h, S.SMRT_OPT_PRECISION, S.SMRT_PREC_F32)
+            S.smrt_set_option(h, S.SMRT_OPT_COLLISION, kind)
+            status, done, chunk = "finite", 0, 1000
+            t0 = time.perf_counter()
+            while done < steps:
+                try:
+                    S.smrt_step(h, chunk)
+                except S.SmrtError as e:
+                    if e.status != S.SMRT_ERR_DIVERGED:
+                        raise
+                    status = "diverged"
+                    done += chunk
+                    break
+                done += chunk
+            sec = time.perf_counter() - t0
+            entry = {"case": name, "n": n, "re": re, "tau": tau, "u_lid": round(u_lid, 6), "collision": kname,
+                     "status": status, "steps": done if status == "finite" else "<= %d" % done,
+                     "seconds": round(sec, 3)}
+            if status == "finite":
+                r1, sums = S.smrt_residual(h)
+                rho = np.empty((n, n))
+                u = np.empty((2, n, n))
+                S.smrt_macros(h, rho, u)
+                S.smrt_step(h, 1000)
+                u2 = np.empty((2, n, n))
+                S.smrt_macros(h, rho, u2)
+                entry.update({"residual_one_step": r1,
+                              "residual_stride_1000": float(np.linalg.norm(u2 - u) / (1000 * np.linalg.norm(u2))),
+                              "mass_rel_change": sums[0] / (n * n) - 1.0,
+                              "max_speed_over_U": float(np.sqrt(u2[0] ** 2 + u2[1] ** 2).max() / u_lid)})
+            S.smrt_destroy(h)
+            out["cases"].append(entry)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def learned_report(args):
     """U-Net warm start: solver-generated steady 256^2 cavities (Re log-uniform in [100, 1e4]), training on
     the GPU with libsmrt's NN kernels, then time-to-steady (stride residual 1e-7) cold vs warm on held-out Re
@@ -623,6 +682,8 @@ def main(argv=None):
         return batched_report(args)
     if args.report == "learned":
         return learned_report(args)
+    if args.report == "paper":
+        return paper_experiments_report(args)
     if args.report == "batched-throughput":
         import torch
         import paper_2409_01076_gb300 as S
