@@ -32,6 +32,16 @@ extern "C" {
 SMRT_API int smrt_nn_gemm(int transA, int transB, int M, int N, int K, float alpha, const void *A, int lda,
                           const void *B, int ldb, float beta, float *C, int ldc, int split_k, void *stream);
 
+/* The same product as smrt_nn_gemm (same arguments and split-K semantics, K >= 1) on the
+ * 5th-generation tensor cores: 128 x 128 output tiles per 128-thread block, operands staged
+ * in shared memory in the no-swizzle K-major core-matrix layout, tcgen05.mma (half x half ->
+ * float32) accumulating in tensor memory, tcgen05.ld epilogue.  Every wait on the tensor core
+ * is bounded: on a timeout the block sets *err = 1 (err: device int, may be NULL), skips its
+ * epilogue and still releases its tensor memory. */
+SMRT_API int smrt_nn_gemm_tc(int transA, int transB, int M, int N, int K, float alpha, const void *A, int lda,
+                             const void *B, int ldb, float beta, float *C, int ldc, int split_k, int *err,
+                             void *stream);
+
 /* 3x3, stride 1, zero padding 1 patches of x (N,H,W,C float32) into
  * col (N*H*W rows x 9*C half, row-major): col[p][(ky*3+kx)*C + c] = x[n][y+ky-1][x+kx-1][c]. */
 SMRT_API int smrt_nn_im2col3(const float *x, int N, int H, int W, int C, void *col, void *stream);

@@ -53,6 +53,8 @@ SIGNATURES = [
     # include/smrt_nn.h
     ("smrt_nn_gemm", c_int, [c_int, c_int, c_int, c_int, c_int, ctypes.c_float, c_void_p, c_int, c_void_p, c_int,
                              ctypes.c_float, c_void_p, c_int, c_int, c_void_p]),
+    ("smrt_nn_gemm_tc", c_int, [c_int, c_int, c_int, c_int, c_int, ctypes.c_float, c_void_p, c_int, c_void_p, c_int,
+                                ctypes.c_float, c_void_p, c_int, c_int, c_void_p, c_void_p]),
     ("smrt_nn_im2col3", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p]),
     ("smrt_nn_col2im3", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p]),
     ("smrt_nn_to_half", c_int, [c_void_p, c_longlong, ctypes.c_float, c_void_p, c_void_p]),

@@ -48,7 +48,16 @@ batch_step_kernel(const typename Prec<PREC>::R *src, typename Prec<PREC>::R *dst
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
         const int2 w = work[t];
         const BatchCav<typename Prec<PREC>::C> &L = cav[w.x];
-        step_block<PREC, KIND, MODE, VEC, BX>(src + L.offset, dst + L.offset, L.p, L.geo, w.y);
+        const StepGeom geo = L.geo;
+        const long long off = L.offset;
+        if (w.y < geo.n_int_blocks) {
+            // interior block: a register copy of the parameters it reads (no moving-wall table),
+            // loaded once per tile
+            const Params<typename Prec<PREC>::C> p = L.p;
+            step_block<PREC, KIND, MODE, VEC, BX>(src + off, dst + off, p, geo, w.y);
+        } else {
+            step_block<PREC, KIND, MODE, VEC, BX>(src + off, dst + off, L.p, geo, w.y);
+        }
     }
 }
 

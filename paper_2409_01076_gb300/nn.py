@@ -30,6 +30,12 @@ def smrt_nn_gemm(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s
                                     _p(B), int(ldb), float(beta), _p(C), int(ldc), int(split_k), _s()))
 
 
+def smrt_nn_gemm_tc(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, split_k=1, err=None):
+    _check(_lib.load().smrt_nn_gemm_tc(int(transA), int(transB), int(M), int(N), int(K), float(alpha), _p(A),
+                                       int(lda), _p(B), int(ldb), float(beta), _p(C), int(ldc), int(split_k),
+                                       _p(err), _s()))
+
+
 def smrt_nn_im2col3(x, col):
     n, h, w, c = x.shape
     _check(_lib.load().smrt_nn_im2col3(_p(x), n, h, w, c, _p(col), _s()))

@@ -1,0 +1,62 @@
+"""smrt_nn_gemm_tc (tcgen05 tensor cores, accumulator in tensor memory) against numpy on the
+same half-rounded operands, and against the WMMA smrt_nn_gemm."""
+import numpy as np
+import pytest
+
+import paper_2409_01076_gb300 as S
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(transA, transB, M, N, K, split, seed):
+    import torch
+    r = np.random.Generator(np.random.PCG64(seed))
+    a = r.normal(size=(K, M) if transA else (M, K)).astype(np.float16)
+    b = r.normal(size=(N, K) if transB else (K, N)).astype(np.float16)
+    c0 = r.normal(size=(M, N)).astype(np.float32)
+    A = torch.tensor(a, device="cuda")
+    B = torch.tensor(b, device="cuda")
+    C = torch.tensor(c0, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    beta = 1.0 if split > 1 else -0.5
+    S.smrt_nn_gemm_tc(transA, transB, M, N, K, 1.5, A, a.shape[1], B, b.shape[1], beta, C, N, split, err)
+    torch.cuda.synchronize()
+    opa = a.astype(np.float64).T if transA else a.astype(np.float64)
+    opb = b.astype(np.float64).T if transB else b.astype(np.float64)
+    ref = 1.5 * opa @ opb + (1.0 if split > 1 else -0.5) * c0
+    return C.cpu().double().numpy(), ref, int(err.item())
+
+
+@pytest.mark.parametrize("transA", [0, 1])
+@pytest.mark.parametrize("transB", [0, 1])
+def test_gemm_tc_single_tile(transA, transB):
+    got, ref, err = _case(transA, transB, 128, 128, 64, 1, 1)
+    assert err == 0
+    assert np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("transA", [0, 1])
+@pytest.mark.parametrize("transB", [0, 1])
+@pytest.mark.parametrize("split", [1, 4])
+def test_gemm_tc_ragged_multi_tile(transA, transB, split):
+    got, ref, err = _case(transA, transB, 300, 200, 520, split, 2 + transA + 2 * transB)
+    assert err == 0
+    assert np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max()
+
+
+def test_gemm_tc_matches_wmma_on_a_conv_shape():
+    """The weight-gradient shape of the top U-Net level: K is the pixel count."""
+    import torch
+    r = np.random.Generator(np.random.PCG64(7))
+    M, N, K = 32, 288, 8192
+    a = torch.tensor(r.normal(size=(K, M)).astype(np.float16), device="cuda")
+    b = torch.tensor(r.normal(size=(K, N)).astype(np.float16), device="cuda")
+    c1 = torch.zeros((M, N), device="cuda")
+    c2 = torch.zeros((M, N), device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    S.smrt_nn_gemm_tc(1, 0, M, N, K, 1.0, a, M, b, N, 1.0, c1, N, 16, err)
+    S.smrt_nn_gemm(1, 0, M, N, K, 1.0, a, M, b, N, 1.0, c2, N, 16)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    d = (c1 - c2).abs().max().item()
+    assert d <= 1e-4 * c2.abs().max().item()
