@@ -33,11 +33,16 @@ SMRT_API int smrt_nn_gemm(int transA, int transB, int M, int N, int K, float alp
                           const void *B, int ldb, float beta, float *C, int ldc, int split_k, void *stream);
 
 /* The same product as smrt_nn_gemm (same arguments and split-K semantics, K >= 1) on the
- * 5th-generation tensor cores: 128 x 128 output tiles per 128-thread block, operands staged
- * in shared memory in the no-swizzle K-major core-matrix layout, tcgen05.mma (half x half ->
- * float32) accumulating in tensor memory, tcgen05.ld epilogue.  Every wait on the tensor core
- * is bounded: on a timeout the block sets *err = 1 (err: device int, may be NULL), skips its
- * epilogue and still releases its tensor memory. */
+ * 5th-generation tensor cores.  transB bit 0 is op(B)'s transpose flag as in smrt_nn_gemm;
+ * bit 1 set stores C^T instead of C (C is then N x M row-major with leading dimension ldc,
+ * and beta / the split-K sums apply to that layout).  Each 128-thread block computes a
+ * 128 x TN output tile (TN = 32, 64 or 128, the smallest that covers N), K in steps of 64
+ * through two shared-memory stages (no-swizzle K-major core-matrix layout) so that the copy
+ * of step k+1 overlaps the tcgen05.mma (half x half -> float32, accumulator in tensor memory)
+ * of step k; tcgen05.ld epilogue.  Every wait on the tensor core is bounded: on a timeout the
+ * block sets *err = 1 (err: device int, may be NULL), skips its epilogue and still releases
+ * its tensor memory.  M == 0 or N == 0 does nothing; SMRT_ERR_ARG for negative M or N, K < 1,
+ * split_k < 1, a NULL operand or a leading dimension smaller than its row. */
 SMRT_API int smrt_nn_gemm_tc(int transA, int transB, int M, int N, int K, float alpha, const void *A, int lda,
                              const void *B, int ldb, float beta, float *C, int ldc, int split_k, int *err,
                              void *stream);
@@ -48,6 +53,11 @@ SMRT_API int smrt_nn_im2col3(const float *x, int N, int H, int W, int C, void *c
 
 /* Adjoint of smrt_nn_im2col3: dx[n][y][x][c] = sum over the 9 patches that read it of dcol (float32). */
 SMRT_API int smrt_nn_col2im3(const float *dcol, int N, int H, int W, int C, float *dx, void *stream);
+
+/* The weights of the adjoint 3x3 convolution: for w (cout, 9 cin) float32 with column
+ * (ky*3+kx)*cin + c, writes wf (cin, 9 cout) half with wf[c][tap*cout + o] = w[o][(8 - tap)*cin + c].
+ * Then dx = im2col3(dz) * wf^T is the input gradient of the convolution (no col2im needed). */
+SMRT_API int smrt_nn_flip3(const float *w, int cout, int cin, void *wf, void *stream);
 
 /* dst[i] = (half)(scale * src[i]), n elements. */
 SMRT_API int smrt_nn_to_half(const float *src, long long n, float scale, void *dst, void *stream);

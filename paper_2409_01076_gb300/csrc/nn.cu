@@ -11,6 +11,7 @@
 
 #include <math.h>
 #include <stdarg.h>
+#include <stdint.h>
 #include <stdio.h>
 
 #include "internal.h"
@@ -110,6 +111,35 @@ __global__ void im2col3_kernel(const float *__restrict__ x, int N, int H, int W,
     }
 }
 
+// C % 8 == 0: one thread per (pixel, tap, 8-channel chunk), two float4 loads, one 16-byte store.
+// Requires N*H*W*9*(C/8) < 2^31.
+__global__ void im2col3_vec_kernel(const float *__restrict__ x, int N, int H, int W, int C, __half *__restrict__ col)
+{
+    const int cc = C >> 3;
+    const int total = N * H * W * 9 * cc;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int chunk = t % cc;
+        const int r = t / cc;
+        const int tap = r % 9;
+        const int p = r / 9;
+        const int xx = p % W, rest = p / W;
+        const int yy = rest % H, n = rest / H;
+        const int sy = yy + tap / 3 - 1, sx = xx + tap % 3 - 1;
+        uint4 out = make_uint4(0, 0, 0, 0);
+        if (sy >= 0 && sy < H && sx >= 0 && sx < W) {
+            const float4 *src = reinterpret_cast<const float4 *>(x + (((size_t)n * H + sy) * W + sx) * C + chunk * 8);
+            const float4 a = src[0], b = src[1];
+            __half2 h0 = __floats2half2_rn(a.x, a.y), h1 = __floats2half2_rn(a.z, a.w);
+            __half2 h2 = __floats2half2_rn(b.x, b.y), h3 = __floats2half2_rn(b.z, b.w);
+            out.x = *reinterpret_cast<unsigned *>(&h0);
+            out.y = *reinterpret_cast<unsigned *>(&h1);
+            out.z = *reinterpret_cast<unsigned *>(&h2);
+            out.w = *reinterpret_cast<unsigned *>(&h3);
+        }
+        reinterpret_cast<uint4 *>(col)[(size_t)p * 9 * cc + (size_t)tap * cc + chunk] = out;
+    }
+}
+
 __global__ void col2im3_kernel(const float *__restrict__ dcol, int N, int H, int W, int C, float *__restrict__ dx)
 {
     const long long total = (long long)N * H * W * C;
@@ -127,6 +157,17 @@ __global__ void col2im3_kernel(const float *__restrict__ dcol, int N, int H, int
             s += dcol[((((size_t)n * H + py) * W + px) * 9 + tap) * C + c];
         }
         dx[t] = s;
+    }
+}
+
+__global__ void flip3_kernel(const float *__restrict__ w, int cout, int cin, __half *__restrict__ wf)
+{
+    const int total = cout * 9 * cin;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int o = t % cout;
+        const int tap = (t / cout) % 9;
+        const int c = t / (9 * cout);
+        wf[t] = __float2half(w[((size_t)o * 9 + (8 - tap)) * cin + c]);   // t = (c * 9 + tap) * cout + o
     }
 }
 
@@ -374,6 +415,11 @@ int smrt_nn_gemm(int transA, int transB, int M, int N, int K, float alpha, const
 int smrt_nn_im2col3(const float *x, int N, int H, int W, int C, void *col, void *stream)
 {
     if (!x || !col || N < 1 || H < 1 || W < 1 || C < 1) return nn_fail(SMRT_ERR_ARG, "smrt_nn_im2col3: bad arguments");
+    const long long chunks = (long long)N * H * W * 9 * (C / 8);
+    if (C % 8 == 0 && chunks < (1LL << 31) && ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(col)) & 15) == 0) {
+        im2col3_vec_kernel<<<grid_for(chunks), 256, 0, (cudaStream_t)stream>>>(x, N, H, W, C, (__half *)col);
+        return launched("smrt_nn_im2col3");
+    }
     im2col3_kernel<<<grid_for((long long)N * H * W * 9 * C), 256, 0, (cudaStream_t)stream>>>(x, N, H, W, C,
                                                                                              (__half *)col);
     return launched("smrt_nn_im2col3");
@@ -384,6 +430,13 @@ int smrt_nn_col2im3(const float *dcol, int N, int H, int W, int C, float *dx, vo
     if (!dcol || !dx || N < 1 || H < 1 || W < 1 || C < 1) return nn_fail(SMRT_ERR_ARG, "smrt_nn_col2im3: bad arguments");
     col2im3_kernel<<<grid_for((long long)N * H * W * C), 256, 0, (cudaStream_t)stream>>>(dcol, N, H, W, C, dx);
     return launched("smrt_nn_col2im3");
+}
+
+int smrt_nn_flip3(const float *w, int cout, int cin, void *wf, void *stream)
+{
+    if (!w || !wf || cout < 1 || cin < 1) return nn_fail(SMRT_ERR_ARG, "smrt_nn_flip3: bad arguments");
+    flip3_kernel<<<grid_for((long long)cout * 9 * cin), 256, 0, (cudaStream_t)stream>>>(w, cout, cin, (__half *)wf);
+    return launched("smrt_nn_flip3");
 }
 
 int smrt_nn_to_half(const float *src, long long n, float scale, void *dst, void *stream)

@@ -1,17 +1,22 @@
 // nn_tc.cu -- smrt_nn_gemm_tc: the GEMM of include/smrt_nn.h on the 5th-generation
 // tensor cores (tcgen05): operands staged in shared memory, accumulator in TMEM.
 //
-// One 128-thread CTA computes a 128 x 128 tile of C.  Per K step of 64:
-//   1. all threads copy op(A)[128 x 64] and op(B)^T[128 x 64] (both K-major) into
-//      shared memory in the no-swizzle core-matrix layout: 8 rows x 16 bytes per
-//      core matrix (128 contiguous bytes), core matrices adjacent in K 128 B apart
-//      (leading byte offset), 8-row groups 1024 B apart (stride byte offset);
+// One 128-thread CTA computes a 128 x TN tile of C (TN = 32, 64 or 128, picked from N).
+// Per K step of 64, double-buffered over two shared-memory stages:
+//   1. all threads copy op(A)[128 x 64] and op(B)^T[TN x 64] (both K-major) into one
+//      stage in the no-swizzle core-matrix layout: 8 rows x 16 bytes per core matrix
+//      (128 contiguous bytes), core matrices adjacent in K 128 B apart (leading byte
+//      offset), 8-row groups 1024 B apart (stride byte offset).  Rows whose K run is
+//      contiguous in global memory move as 16-byte vectors; transposed operands move as
+//      16-byte vectors along M (or N) scattered into eight core-matrix rows;
 //   2. fence.proxy.async makes those generic-proxy writes visible to the tensor core;
-//   3. thread 0 issues four tcgen05.mma (M 128, N 128, K 16, half x half -> f32)
-//      and commits them to an mbarrier;
-//   4. every thread waits on the mbarrier (bounded: a timeout sets *err and the CTA
-//      stops issuing, still releasing its TMEM) before the buffers are refilled.
-// Epilogue: warp w reads TMEM lanes 32w..32w+31 (rows of the tile) with tcgen05.ld.
+//   3. thread 0 issues four tcgen05.mma (M 128, N TN, K 16, half x half -> f32) and
+//      commits them to that stage's mbarrier;
+//   4. before a stage is refilled, every thread waits on its mbarrier (bounded: a
+//      timeout sets *err, waits once more with a limit, and the CTA still releases
+//      its TMEM), so the copy of one stage overlaps the MMAs of the other.
+// Epilogue: warp w reads TMEM lanes 32w..32w+31 (rows of the tile) with tcgen05.ld and
+// writes C, or C^T when trans_c is set.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -24,8 +29,7 @@
 
 namespace {
 
-constexpr int TM = 128, TN = 128, TK = 64;
-constexpr uint32_t kTmemCols = 128;
+constexpr int TM = 128, TK = 64;
 constexpr long long kWaitLimit = 1LL << 24;   // try_wait polls before a CTA gives up
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
@@ -33,7 +37,7 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p)
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Offset (in halves) of element (row, k) of a 128 x 64 K-major tile in the core-matrix layout.
+// Offset (in halves) of element (row, k) of a rows x 64 K-major tile in the core-matrix layout.
 __device__ __forceinline__ int core_offset(int row, int k)
 {
     return ((row >> 3) * (TK / 8) + (k >> 3)) * 64 + (row & 7) * 8 + (k & 7);
@@ -52,18 +56,88 @@ __device__ __forceinline__ unsigned long long make_desc(uint32_t saddr, uint32_t
     return d;
 }
 
-// Instruction descriptor of kind::f16: D f32, A and B half, both K-major, N = 128, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | (0u << 15) | (0u << 16) |
-                            ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+// Instruction descriptor of kind::f16: D f32, A and B half, both K-major, N = TN, M = 128.
+template <int TN>
+__host__ __device__ constexpr uint32_t idesc()
+{
+    return (1u << 4) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
 
+__device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t phase)
+{
+    uint32_t done = 0;
+    for (long long it = 0; it < kWaitLimit && !done; ++it) {
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(mb), "r"(phase) : "memory");
+    }
+    return done != 0;
+}
+
+// Copy rows [r0, r0 + ROWS) x k [k0, k0 + 64) of op(X) into a K-major core-matrix tile.
+// kmajor: X stores each row's K run contiguously (X[row * ld + k]); otherwise X stores
+// op(X)^T (X[k * ld + row]).  vec: 16-byte vectors are allowed (ld % 8 == 0).
+template <int ROWS>
+__device__ __forceinline__ void load_tile(__half *tile, const __half *__restrict__ X, int ld, bool kmajor, bool vec,
+                                          int r0, int nrows, int k0, int kend)
+{
+    const int tid = threadIdx.x;
+    const __half zero = __float2half(0.0f);
+    if (vec) {
+        // ROWS x 8 chunks of 8 halves; a chunk runs along K (kmajor) or along rows (transposed)
+        for (int c = tid; c < ROWS * (TK / 8); c += 128) {
+            if (kmajor) {
+                const int r = c / (TK / 8), kc = (c % (TK / 8)) * 8;
+                const int row = r0 + r, k = k0 + kc;
+                uint4 v = make_uint4(0, 0, 0, 0);
+                if (row < nrows && k + 8 <= kend) {
+                    v = *reinterpret_cast<const uint4 *>(X + (size_t)row * ld + k);
+                } else if (row < nrows) {
+                    __half h[8];
+                    #pragma unroll
+                    for (int j = 0; j < 8; ++j) h[j] = (k + j < kend) ? X[(size_t)row * ld + k + j] : zero;
+                    v = *reinterpret_cast<uint4 *>(h);
+                }
+                *reinterpret_cast<uint4 *>(tile + core_offset(r, kc)) = v;
+            } else {
+                const int kk = c / (ROWS / 8), rc = (c % (ROWS / 8)) * 8;
+                const int row = r0 + rc, k = k0 + kk;
+                __half h[8];
+                if (k < kend && row + 8 <= nrows) {
+                    *reinterpret_cast<uint4 *>(h) = *reinterpret_cast<const uint4 *>(X + (size_t)k * ld + row);
+                } else {
+                    #pragma unroll
+                    for (int j = 0; j < 8; ++j) h[j] = (k < kend && row + j < nrows) ? X[(size_t)k * ld + row + j] : zero;
+                }
+                #pragma unroll
+                for (int j = 0; j < 8; ++j) tile[core_offset(rc + j, kk)] = h[j];
+            }
+        }
+        return;
+    }
+    for (int idx = tid; idx < ROWS * TK; idx += 128) {
+        int r, kk;
+        if (kmajor) { r = idx / TK; kk = idx % TK; }
+        else { kk = idx / ROWS; r = idx % ROWS; }
+        const int row = r0 + r, k = k0 + kk;
+        __half v = zero;
+        if (row < nrows && k < kend) v = kmajor ? X[(size_t)row * ld + k] : X[(size_t)k * ld + row];
+        tile[core_offset(r, kk)] = v;
+    }
+}
+
+template <int TN>
 __global__ void __launch_bounds__(128)
 gemm_tc_kernel(int transA, int transB, int M, int N, int K, float alpha, const __half *__restrict__ A, int lda,
-               const __half *__restrict__ B, int ldb, float beta, float *C, int ldc, int k_chunk, int atomic,
-               int *err)
+               const __half *__restrict__ B, int ldb, float beta, float *C, int ldc, int trans_c, int k_chunk,
+               int atomic, int vec_a, int vec_b, int *err)
 {
-    __shared__ __align__(1024) __half sA[TM * TK];
-    __shared__ __align__(1024) __half sB[TN * TK];
-    __shared__ __align__(8) unsigned long long mbar;
+    constexpr uint32_t kCols = TN;          // TMEM columns: one f32 column per output column
+    // dynamic shared memory: two stages of A (128 x 64) then two of B (TN x 64), 1024-byte aligned
+    extern __shared__ __align__(1024) unsigned char dyn[];
+    __half(*sA)[TM * TK] = reinterpret_cast<__half(*)[TM * TK]>(dyn);
+    __half(*sB)[TN * TK] = reinterpret_cast<__half(*)[TN * TK]>(dyn + 2 * TM * TK * sizeof(__half));
+    __shared__ __align__(8) unsigned long long mbar[2];
     __shared__ uint32_t tmem_holder;
     __shared__ int failed;
 
@@ -74,84 +148,70 @@ gemm_tc_kernel(int transA, int transB, int M, int N, int K, float alpha, const _
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_addr(&tmem_holder)), "r"(kTmemCols));
+                     :: "r"(smem_addr(&tmem_holder)), "r"(kCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&mbar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&mbar[1])));
         failed = 0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_holder;
-    const uint32_t sa = smem_addr(sA), sb = smem_addr(sB), mb = smem_addr(&mbar);
-    const __half zero = __float2half(0.0f);
 
-    uint32_t phase = 0;
-    bool any = false;
-    for (int k0 = kbeg; k0 < kend; k0 += TK) {
-        for (int idx = tid; idx < TM * TK; idx += 128) {
-            int r, kk;
-            if (!transA) { r = idx / TK; kk = idx % TK; }
-            else { kk = idx / TM; r = idx % TM; }
-            const int m = m0 + r, k = k0 + kk;
-            __half v = zero;
-            if (m < M && k < kend) v = transA ? A[(size_t)k * lda + m] : A[(size_t)m * lda + k];
-            sA[core_offset(r, kk)] = v;
+    uint32_t phase[2] = {0u, 0u};
+    bool pending[2] = {false, false};
+    int step = 0;
+    for (int k0 = kbeg; k0 < kend; k0 += TK, ++step) {
+        const int s = step & 1;
+        if (pending[s]) {           // the MMAs that read this stage two steps ago must be done
+            if (!mbar_wait(smem_addr(&mbar[s]), phase[s])) {
+                failed = 1;
+                if (err) atomicExch(err, 1);
+                mbar_wait(smem_addr(&mbar[s]), phase[s]);
+            }
+            phase[s] ^= 1u;
+            pending[s] = false;
         }
-        for (int idx = tid; idx < TN * TK; idx += 128) {
-            int r, kk;
-            if (transB) { r = idx / TK; kk = idx % TK; }
-            else { kk = idx / TN; r = idx % TN; }
-            const int n = n0 + r, k = k0 + kk;
-            __half v = zero;
-            if (n < N && k < kend) v = transB ? B[(size_t)n * ldb + k] : B[(size_t)k * ldb + n];
-            sB[core_offset(r, kk)] = v;
-        }
+        load_tile<TM>(sA[s], A, lda, !transA, vec_a, m0, M, k0, kend);
+        load_tile<TN>(sB[s], B, ldb, transB, vec_b, n0, N, k0, kend);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (failed) break;
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t sa = smem_addr(sA[s]), sb = smem_addr(sB[s]);
             #pragma unroll
             for (int kk = 0; kk < TK / 16; ++kk) {
                 const unsigned long long ad = make_desc(sa + kk * 256, 128, (TK / 8) * 128);
                 const unsigned long long bd = make_desc(sb + kk * 256, 128, (TK / 8) * 128);
-                const uint32_t acc = (any || kk > 0) ? 1u : 0u;
+                const uint32_t acc = (step > 0 || kk > 0) ? 1u : 0u;
                 asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-                             :: "r"(tmem), "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+                             :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc<TN>()), "r"(acc));
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(mb) : "memory");
+                         :: "r"(smem_addr(&mbar[s])) : "memory");
         }
-        any = true;
-        // wait until the MMAs have consumed the tiles (bounded)
-        uint32_t done = 0;
-        for (long long it = 0; it < kWaitLimit && !done; ++it) {
-            asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                         "selp.u32 %0, 1, 0, p;\n\t}"
-                         : "=r"(done) : "r"(mb), "r"(phase) : "memory");
-        }
-        if (!done) {
+        pending[s] = true;
+    }
+    // drain: the last commits cover every MMA issued
+    for (int s = 0; s < 2; ++s) {
+        if (!pending[s]) continue;
+        if (!mbar_wait(smem_addr(&mbar[s]), phase[s])) {
             failed = 1;
             if (err) atomicExch(err, 1);
-            // give the MMAs in flight a second bounded chance to finish before TMEM is released
-            for (long long it = 0; it < kWaitLimit && !done; ++it) {
-                asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                             "selp.u32 %0, 1, 0, p;\n\t}"
-                             : "=r"(done) : "r"(mb), "r"(phase) : "memory");
-            }
+            mbar_wait(smem_addr(&mbar[s]), phase[s]);
         }
-        phase ^= 1u;
-        __syncthreads();
-        if (failed) break;
     }
+    __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
 
     if (!failed) {
         const int row = m0 + warp * 32 + lane;
+        const bool any = kend > kbeg;
         #pragma unroll 1
         for (int c = 0; c < TN; c += 32) {
             uint32_t r[32];
@@ -172,7 +232,7 @@ gemm_tc_kernel(int transA, int transB, int M, int N, int K, float alpha, const _
                     const int n = n0 + c + j;
                     if (n >= N) break;
                     const float v = alpha * (any ? __uint_as_float(r[j]) : 0.0f);
-                    float *cp = C + (size_t)row * ldc + n;
+                    float *cp = trans_c ? C + (size_t)n * ldc + row : C + (size_t)row * ldc + n;
                     if (atomic) atomicAdd(cp, v);
                     else *cp = (beta != 0.0f) ? v + beta * *cp : v;
                 }
@@ -181,7 +241,7 @@ gemm_tc_kernel(int transA, int transB, int M, int N, int K, float alpha, const _
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTmemCols));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kCols));
 }
 
 int tc_fail(int code, const char *fmt, ...)
@@ -195,26 +255,50 @@ int tc_fail(int code, const char *fmt, ...)
     return code;
 }
 
+template <int TN>
+cudaError_t launch_tc(int transA, int transB, int M, int N, int K, float alpha, const void *A, int lda, const void *B,
+                      int ldb, float beta, float *C, int ldc, int trans_c, int split_k, int *err, cudaStream_t s)
+{
+    int chunk = (K + split_k - 1) / split_k;
+    chunk = ((chunk + TK - 1) / TK) * TK;
+    const int splits = (K + chunk - 1) / chunk;
+    dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, splits);
+    if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
+    const int aligned_a = (lda % 8 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
+    const int aligned_b = (ldb % 8 == 0) && ((reinterpret_cast<uintptr_t>(B) & 15) == 0);
+    const size_t smem = 2 * (size_t)(TM + TN) * TK * sizeof(__half);
+    static bool attr_set = false;       // per instantiation; the attribute is per function
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    gemm_tc_kernel<TN><<<grid, 128, smem, s>>>(transA, transB, M, N, K, alpha, (const __half *)A, lda,
+                                            (const __half *)B, ldb, beta, C, ldc, trans_c, chunk,
+                                            split_k > 1 ? 1 : 0, aligned_a, aligned_b, err);
+    return cudaGetLastError();
+}
+
 } // namespace
 
 extern "C" int smrt_nn_gemm_tc(int transA, int transB, int M, int N, int K, float alpha, const void *A, int lda,
                                const void *B, int ldb, float beta, float *C, int ldc, int split_k, int *err,
                                void *stream)
 {
-    if (M < 0 || N < 0 || K < 1 || !A || !B || !C || split_k < 1 || ldc < N || lda < (transA ? M : K) ||
-        ldb < (transB ? K : N))
+    // transB bit 1 (value 2 | transB) requests the transposed store C^T (N x M, leading dimension ldc)
+    const int trans_c = (transB >> 1) & 1;
+    transB &= 1;
+    if (M < 0 || N < 0 || K < 1 || !A || !B || !C || split_k < 1 || ldc < (trans_c ? M : N) ||
+        lda < (transA ? M : K) || ldb < (transB ? K : N))
         return tc_fail(SMRT_ERR_ARG, "smrt_nn_gemm_tc: bad arguments (M %d N %d K %d lda %d ldb %d ldc %d split %d)",
                        M, N, K, lda, ldb, ldc, split_k);
     if (M == 0 || N == 0) return SMRT_OK;
-    int chunk = (K + split_k - 1) / split_k;
-    chunk = ((chunk + TK - 1) / TK) * TK;
-    const int splits = (K + chunk - 1) / chunk;
-    dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, splits);
-    if (grid.y > 65535 || grid.z > 65535) return tc_fail(SMRT_ERR_ARG, "smrt_nn_gemm_tc: M or split_k too large");
-    gemm_tc_kernel<<<grid, 128, 0, (cudaStream_t)stream>>>(transA, transB, M, N, K, alpha, (const __half *)A, lda,
-                                                           (const __half *)B, ldb, beta, C, ldc, chunk,
-                                                           split_k > 1 ? 1 : 0, err);
-    cudaError_t e = cudaGetLastError();
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if (N <= 32) e = launch_tc<32>(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, trans_c, split_k, err, s);
+    else if (N <= 64) e = launch_tc<64>(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, trans_c, split_k, err, s);
+    else e = launch_tc<128>(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, trans_c, split_k, err, s);
     if (e != cudaSuccess) return tc_fail(SMRT_ERR_CUDA, "smrt_nn_gemm_tc: %s", cudaGetErrorString(e));
     return SMRT_OK;
 }

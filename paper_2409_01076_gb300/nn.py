@@ -46,6 +46,11 @@ def smrt_nn_col2im3(dcol, shape, dx):
     _check(_lib.load().smrt_nn_col2im3(_p(dcol), n, h, w, c, _p(dx), _s()))
 
 
+def smrt_nn_flip3(w, wf):
+    cout, k9 = w.shape
+    _check(_lib.load().smrt_nn_flip3(_p(w), int(cout), int(k9 // 9), _p(wf), _s()))
+
+
 def smrt_nn_to_half(src, dst, scale=1.0):
     _check(_lib.load().smrt_nn_to_half(_p(src), src.numel(), float(scale), _p(dst), _s()))
 

@@ -47,7 +47,8 @@ def re_feature(re: float) -> float:
 
 
 class UNet:
-    def __init__(self, base: int = 32, cin: int = 3, cout: int = 3, seed: int = 0, device: str = "cuda"):
+    def __init__(self, base: int = 32, cin: int = 3, cout: int = 3, seed: int = 0, device: str = "cuda",
+                 gemm: str = "tcgen05"):
         import torch
         self.torch = torch
         self.base, self.cin, self.cout, self.device = base, cin, cout, device
@@ -71,6 +72,20 @@ class UNet:
         self.grad_scale = 2.0 ** 16
         self._found_inf = torch.zeros(1, dtype=torch.int32, device=device)
         self._loss = torch.zeros(1, dtype=torch.float64, device=device)
+        if gemm not in ("tcgen05", "wmma"):
+            raise ValueError("gemm must be 'tcgen05' or 'wmma'")
+        self.gemm_backend = gemm
+        self._gemm_err = torch.zeros(1, dtype=torch.int32, device=device)   # tensor-core wait timeouts
+
+    def _gemm(self, transA, transB, M, N, Kd, alpha, A, lda, B, ldb, beta, C, ldc, split=1):
+        if self.gemm_backend == "tcgen05":
+            K.smrt_nn_gemm_tc(transA, transB, M, N, Kd, alpha, A, lda, B, ldb, beta, C, ldc, split, self._gemm_err)
+        else:
+            K.smrt_nn_gemm(transA, transB, M, N, Kd, alpha, A, lda, B, ldb, beta, C, ldc, split)
+
+    def gemm_timeouts(self) -> int:
+        """Number of tensor-core wait timeouts seen so far (0 unless the hardware stalled)."""
+        return int(self._gemm_err.item())
 
     # ---- parameters --------------------------------------------------------------------
     def load_numpy(self, params: dict) -> None:
@@ -86,12 +101,16 @@ class UNet:
     # ---- one convolution (3x3 via im2col, or 1x1) ----------------------------------------
     def _half_weights(self):
         t = self.torch
-        self._wh = {}
+        self._wh, self._wf = {}, {}
         for name, ci, co, k, _ in self.specs:
             w = self.params[name + ".w"]
             h = t.empty(w.shape, dtype=t.float16, device=self.device)
             K.smrt_nn_to_half(w, h)
             self._wh[name] = h
+            if k == 3 and name != "enc1a":      # weights of the adjoint convolution (input gradient)
+                f = t.empty((ci, 9 * co), dtype=t.float16, device=self.device)
+                K.smrt_nn_flip3(w, f)
+                self._wf[name] = f
 
     def _conv(self, spec, x, cache):
         t = self.torch
@@ -105,7 +124,7 @@ class UNet:
         else:
             K.smrt_nn_to_half(x, col)
         y = t.empty((n, h, w, co), dtype=t.float32, device=self.device)
-        K.smrt_nn_gemm(0, 1, rows, co, kk, 1.0, col, kk, self._wh[name], kk, 0.0, y, co)
+        self._gemm(0, 1, rows, co, kk, 1.0, col, kk, self._wh[name], kk, 0.0, y, co)
         z = t.empty_like(y) if (act and cache is not None) else None
         K.smrt_nn_bias_act(y, self.params[name + ".b"], act, z, y)
         if cache is not None:
@@ -124,15 +143,22 @@ class UNet:
         dzh = t.empty(dz.shape, dtype=t.float16, device=self.device)
         K.smrt_nn_to_half(dz, dzh)
         split = max(1, min(256, rows // 8192))
-        K.smrt_nn_gemm(1, 0, co, kk, rows, 1.0, dzh, co, col, kk, 1.0, self.grads[name + ".w"], kk, split)
+        gw = self.grads[name + ".w"]
+        if self.gemm_backend == "tcgen05":
+            # dW^T = col^T dz: the 9 cin dimension on the tensor core's M = 128 side, stored transposed
+            K.smrt_nn_gemm_tc(1, 2, kk, co, rows, 1.0, col, kk, dzh, co, 1.0, gw, kk, split, self._gemm_err)
+        else:
+            self._gemm(1, 0, co, kk, rows, 1.0, dzh, co, col, kk, 1.0, gw, kk, split)
         if not need_dx:
             return None
-        dcol = t.empty((rows, kk), dtype=t.float32, device=self.device)
-        K.smrt_nn_gemm(0, 0, rows, kk, co, 1.0, dzh, co, self._wh[name], kk, 0.0, dcol, kk)
-        if k == 1:
-            return dcol.view(xshape)
         dx = t.empty(xshape, dtype=t.float32, device=self.device)
-        K.smrt_nn_col2im3(dcol, xshape, dx)
+        if k == 1:
+            self._gemm(0, 0, rows, ci, co, 1.0, dzh, co, self._wh[name], ci, 0.0, dx, ci)
+            return dx
+        # dx = im2col(dz) * flip(W)^T: the adjoint 3x3 convolution, no col2im
+        dzcol = t.empty((rows, 9 * co), dtype=t.float16, device=self.device)
+        K.smrt_nn_im2col3(dz.view(n, h, w, co), dzcol)
+        self._gemm(0, 1, rows, ci, 9 * co, 1.0, dzcol, 9 * co, self._wf[name], 9 * co, 0.0, dx, ci)
         return dx
 
     # ---- the network ------------------------------------------------------------------

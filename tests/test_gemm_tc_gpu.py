@@ -60,3 +60,51 @@ def test_gemm_tc_matches_wmma_on_a_conv_shape():
     assert int(err.item()) == 0
     d = (c1 - c2).abs().max().item()
     assert d <= 1e-4 * c2.abs().max().item()
+
+
+@pytest.mark.parametrize("N", [20, 50, 200])
+@pytest.mark.parametrize("trans_c", [0, 1])
+@pytest.mark.parametrize("transA,transB", [(0, 1), (1, 0)])
+def test_gemm_tc_tile_widths_and_transposed_store(N, trans_c, transA, transB):
+    """32-, 64- and 128-wide tiles; C or C^T stored; odd K (scalar copy path) and even K (vector path)."""
+    import torch
+    for K in (27, 264):
+        r = np.random.Generator(np.random.PCG64(N + K + 7 * trans_c))
+        M = 200
+        a = r.normal(size=(K, M) if transA else (M, K)).astype(np.float16)
+        b = r.normal(size=(N, K) if transB else (K, N)).astype(np.float16)
+        opa = a.astype(np.float64).T if transA else a.astype(np.float64)
+        opb = b.astype(np.float64).T if transB else b.astype(np.float64)
+        ref = opa @ opb
+        C = torch.zeros((N, M) if trans_c else (M, N), device="cuda")
+        err = torch.zeros(1, dtype=torch.int32, device="cuda")
+        S.smrt_nn_gemm_tc(transA, transB | (2 * trans_c), M, N, K, 1.0, torch.tensor(a, device="cuda"), a.shape[1],
+                          torch.tensor(b, device="cuda"), b.shape[1], 0.0, C, M if trans_c else N, 1, err)
+        torch.cuda.synchronize()
+        got = C.cpu().double().numpy()
+        if trans_c:
+            got = got.T
+        assert int(err.item()) == 0
+        assert np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max(), (K, N)
+
+
+def test_flip3_is_the_adjoint_convolution_weight():
+    """<conv(x, W), dz> = <x, conv(dz, flip(W))> on a small zero-padded lattice."""
+    import torch
+    from oracle import unet_oracle as U
+    r = np.random.Generator(np.random.PCG64(11))
+    cout, cin = 5, 3
+    w = r.normal(size=(cout, 9 * cin))
+    wf = torch.empty((cin, 9 * cout), dtype=torch.float16, device="cuda")
+    S.smrt_nn_flip3(torch.tensor(w, dtype=torch.float32, device="cuda"), wf)
+    torch.cuda.synchronize()
+    f = wf.cpu().double().numpy()
+    for c in range(cin):
+        for tap in range(9):
+            for o in range(cout):
+                assert f[c, tap * cout + o] == np.float16(w[o, (8 - tap) * cin + c])
+    x = r.normal(size=(1, 6, 5, cin))
+    dz = r.normal(size=(1, 6, 5, cout))
+    y = (U.im2col3(x) @ w.T).reshape(1, 6, 5, cout)
+    dx = (U.im2col3(dz) @ f.T).reshape(1, 6, 5, cin)
+    assert abs((y * dz).sum() - (x * dx).sum()) < 1e-2 * np.abs(y * dz).sum()

@@ -154,7 +154,8 @@ def test_resize_bilinear_special_cases():
     assert np.abs(_np(out)[:, inner, inner] - ref[:, inner, inner]).max() < 1e-5
 
 
-def test_unet_loss_and_gradients_match_oracle():
+@pytest.mark.parametrize("backend", ["tcgen05", "wmma"])
+def test_unet_loss_and_gradients_match_oracle(backend):
     """Same weights, same batch: loss and every gradient tensor within half-precision operand rounding."""
     from paper_2409_01076_gb300.unet import UNet
     base, n, h, w = 8, 2, 16, 16
@@ -163,7 +164,7 @@ def test_unet_loss_and_gradients_match_oracle():
     x = r.uniform(0, 1, size=(n, h, w, 3))
     t = 0.3 * r.normal(size=(n, h, w, 3))
     loss_ref, grads_ref, _ = U.loss_and_grads(params, x, t, base)
-    net = UNet(base=base)
+    net = UNet(base=base, gemm=backend)
     net.load_numpy(params)
     net.grad_scale = 1024.0
     net.loss_and_grad(_t(x), _t(t))
@@ -174,6 +175,8 @@ def test_unet_loss_and_gradients_match_oracle():
         rel = np.linalg.norm(g - gr) / max(np.linalg.norm(gr), 1e-30)
         cos = (g * gr).sum() / max(np.linalg.norm(g) * np.linalg.norm(gr), 1e-30)
         assert rel < 3e-2 and cos > 0.999, (key, rel, cos)
+    if backend == "tcgen05":
+        assert net.gemm_timeouts() == 0
 
 
 def test_unet_training_reduces_the_loss():
