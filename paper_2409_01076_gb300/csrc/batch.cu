@@ -38,26 +38,64 @@ constexpr int kResTile = 256;
 
 // counts[0] = active lattices, counts[1] = total step blocks, counts[2] = total residual tiles.
 // work[t] = (lattice, block of that lattice) for step block t of the concatenated list.
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
+{
+    const unsigned int d = static_cast<unsigned int>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
 template <int PREC, int KIND, int MODE, int VEC, int BX>
-__global__ void __launch_bounds__(BX)
+__global__ void __launch_bounds__(BX, 1024 / BX)   // at most 64 registers: 1024 resident threads per SM
 batch_step_kernel(const typename Prec<PREC>::R *src, typename Prec<PREC>::R *dst,
                   const BatchCav<typename Prec<PREC>::C> *__restrict__ cav, const int2 *__restrict__ work,
                   const int *__restrict__ counts)
 {
+    using Cav = BatchCav<typename Prec<PREC>::C>;
+    static_assert(sizeof(Cav) % 8 == 0 && alignof(Cav) >= 8, "lattice record copied in 8-byte words");
+    constexpr int kWords = (int)(sizeof(Cav) / 8);
+    // The lattice record of the running tile sits in shared memory (buffer `buf`).  The work list
+    // is read two tiles ahead; when the next tile belongs to another lattice its record is copied
+    // into the other buffer with cp.async while this tile runs.  So neither the work list nor the
+    // record is a dependent load in front of a tile's population loads, and the block
+    // synchronises only where its walk crosses from one lattice to another.
+    __shared__ __align__(16) unsigned long long rec[2][kWords];
     const int total = counts[1];
-    for (int t = blockIdx.x; t < total; t += gridDim.x) {
-        const int2 w = work[t];
-        const BatchCav<typename Prec<PREC>::C> &L = cav[w.x];
-        const StepGeom geo = L.geo;
-        const long long off = L.offset;
-        if (w.y < geo.n_int_blocks) {
-            // interior block: a register copy of the parameters it reads (no moving-wall table),
-            // loaded once per tile
-            const Params<typename Prec<PREC>::C> p = L.p;
-            step_block<PREC, KIND, MODE, VEC, BX>(src + off, dst + off, p, geo, w.y);
-        } else {
-            step_block<PREC, KIND, MODE, VEC, BX>(src + off, dst + off, L.p, geo, w.y);
+    const int G = gridDim.x;
+    int t = blockIdx.x;
+    if (t >= total) return;
+    int2 w = work[t];
+    for (int k = threadIdx.x; k < kWords; k += BX)
+        rec[0][k] = reinterpret_cast<const unsigned long long *>(cav + w.x)[k];
+    __syncthreads();
+    int buf = 0;
+    int tn = t + G;
+    int2 wn = (tn < total) ? work[tn] : w;
+    for (;;) {
+        const int tnn = tn + G;
+        const int2 wnn = (tnn < total) ? work[tnn] : wn;
+        const bool next = tn < total;
+        const bool swap = next && wn.x != w.x;          // block-uniform
+        if (swap) {
+            const unsigned long long *g = reinterpret_cast<const unsigned long long *>(cav + wn.x);
+            for (int k = threadIdx.x; k < kWords; k += BX) cp_async8(&rec[buf ^ 1][k], g + k);
         }
+        const Cav &r = *reinterpret_cast<const Cav *>(rec[buf]);
+        step_block<PREC, KIND, MODE, VEC, BX>(src + r.offset, dst + r.offset, r.p, r.geo, w.y);
+        if (!next) break;
+        if (swap) {
+            cp_async_wait_all();
+            __syncthreads();                           // the new record is visible to every thread
+            buf ^= 1;
+        }
+        t = tn;
+        w = wn;
+        tn = tnn;
+        wn = wnn;
     }
 }
 
