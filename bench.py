@@ -56,6 +56,7 @@ def parse_args(argv=None):
     p.add_argument("--learned-cap-1024", type=int, default=1000000)
     p.add_argument("--batch-count", type=int, default=512)
     p.add_argument("--batch-sides", default="64,128,256,512,1024")
+    p.add_argument("--batch-re", default="100,5000", help="Re range (log-uniform) of the batched reports")
     p.add_argument("--tol", type=float, default=1e-7)
     p.add_argument("--residual", choices=["stride", "step"], default="stride",
                    help="batched report: stride (mean change per update over a check) or one-step residual")
@@ -485,10 +486,10 @@ def gpu_arm(args):
     return 0
 
 
-def batched_setup(S, count=512, seed=0, layout="ab", sides=(64, 128, 256, 512, 1024)):
+def batched_setup(S, count=512, seed=0, layout="ab", sides=(64, 128, 256, 512, 1024), re=(100.0, 5000.0)):
     """The seeded uneven batch: sides uniform over {64..1024}, Re log-uniform in [100, 5000], U_lid = 0.1."""
     from paper_2409_01076_gb300 import workloads as W
-    cav = W.batched_cavities(count, seed, sides=tuple(sides))
+    cav = W.batched_cavities(count, seed, sides=tuple(sides), re_lo=re[0], re_hi=re[1])
     nx = [n for n, _ in cav]
     taus = [W.cavity_tau(n, 0.1, re) for n, re in cav]
     b = S.smrt_batch_create(nx, nx, taus, [0.1] * count, W.CAVITY, S.SMRT_PREC_F32,
@@ -496,22 +497,29 @@ def batched_setup(S, count=512, seed=0, layout="ab", sides=(64, 128, 256, 512, 1
     return b, cav
 
 
-def batched_throughput(S, steps, layout="ab", count=512, sides=(64, 128, 256, 512, 1024)):
+def batched_throughput(S, steps, layout="ab", count=512, sides=(64, 128, 256, 512, 1024), re=(100.0, 5000.0)):
+    """MLUPS of smrt_batch_step over the lattices active when the timed call starts (a lattice that
+    diverges is still updated until the call returns, and retired after it)."""
+    import numpy as np
     import torch
-    b, cav = batched_setup(S, count=count, layout=layout, sides=sides)
-    nodes = S.smrt_batch_nodes(b)
+    b, cav = batched_setup(S, count=count, layout=layout, sides=sides, re=re)
     choice = S.smrt_batch_autotune(b, 10)
     S.smrt_batch_step(b, 4)
     torch.cuda.synchronize()
+    side = np.array([n for n, _ in cav], dtype=np.int64)
+    active = S.smrt_batch_status(b)[2] == S.SMRT_BATCH_ACTIVE
+    nodes = int((side[active] ** 2).sum())
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     S.smrt_batch_step(b, steps)
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    after = int((S.smrt_batch_status(b)[2] == S.SMRT_BATCH_ACTIVE).sum())
     S.smrt_batch_destroy(b)
     return {"mlups": round(nodes * steps / (ms * 1e-3) / 1e6, 1), "ms_per_step": round(ms / steps, 5),
             "hbm_gbs": round(72 * nodes / (ms / steps * 1e-3) / 1e9, 1), "steps": steps, "cavities": len(cav),
+            "active": int(active.sum()), "active_after": after, "re": list(re),
             "nodes": nodes, "tile_shape_choice": choice, "layout": layout}
 
 
@@ -522,7 +530,7 @@ def batched_report(args):
     import paper_2409_01076_gb300 as S
     torch.cuda.set_device(0)
     S._lib.load()
-    b, cav = batched_setup(S, count=args.batch_count, layout=args.layout, sides=_sides(args))
+    b, cav = batched_setup(S, count=args.batch_count, layout=args.layout, sides=_sides(args), re=_re(args))
     nodes = S.smrt_batch_nodes(b)
     t0 = time.perf_counter()
     choice = S.smrt_batch_autotune(b, 10)
@@ -743,7 +751,7 @@ def main(argv=None):
         import paper_2409_01076_gb300 as S
         torch.cuda.set_device(0)
         S._lib.load()
-        out = batched_throughput(S, args.steps, args.layout, args.batch_count, _sides(args))
+        out = batched_throughput(S, args.steps, args.layout, args.batch_count, _sides(args), _re(args))
         out["report"] = "batched-throughput"
         print(json.dumps(out), flush=True)
         return 0
@@ -752,6 +760,11 @@ def main(argv=None):
 
 def _sides(args):
     return tuple(int(s) for s in args.batch_sides.split(","))
+
+
+def _re(args):
+    lo, hi = (float(s) for s in args.batch_re.split(","))
+    return lo, hi
 
 
 if __name__ == "__main__":

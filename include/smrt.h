@@ -243,11 +243,17 @@ SMRT_API int smrt_batch_create(int count, const int *nx, const int *ny, const do
 /* Stream for every later launch and copy (NULL: legacy default stream). */
 SMRT_API int smrt_batch_set_stream(smrt_batch_t *b, void *stream);
 
-/* Times each candidate tile shape (nodes per thread x threads per block) of the
- * work-list kernel on `steps` steps of this batch, run on a copy of the state so
- * no lattice advances, and keeps the fastest; *choice (may be NULL) receives its
- * index.  Allocates one scratch copy of the populations for the duration. */
+/* Times each candidate tile shape of the work-list kernel (nodes per thread x
+ * threads per block, with or without a 64-register bound; FP32 storage: 5
+ * candidates, FP64: 4) on `steps` steps of this batch, run on a copy of the state
+ * so no lattice advances, and keeps the fastest; *choice (may be NULL) receives
+ * its index.  Allocates one scratch copy of the populations for the duration. */
 SMRT_API int smrt_batch_autotune(smrt_batch_t *b, int steps, int *choice);
+
+/* Selects tile shape `shape` (an index as returned by smrt_batch_autotune) without
+ * timing anything; SMRT_ERR_ARG if it is not a candidate of the batch's precision.
+ * The lattices' state is untouched: every shape computes the same bits. */
+SMRT_API int smrt_batch_set_shape(smrt_batch_t *b, int shape);
 
 /* n >= 0 updates of every active lattice (one work-list launch each); waits,
  * then marks lattices whose divergence word is set as SMRT_BATCH_DIVERGED. */

@@ -247,6 +247,10 @@ def smrt_batch_autotune(b: BatchHandle, steps: int = 10) -> int:
     return choice.value
 
 
+def smrt_batch_set_shape(b: BatchHandle, shape: int) -> None:
+    _bcheck(_lib.load().smrt_batch_set_shape(b, int(shape)), b)
+
+
 def smrt_batch_step(b: BatchHandle, n: int) -> None:
     _bcheck(_lib.load().smrt_batch_step(b, int(n)), b)
 

@@ -41,6 +41,7 @@ SIGNATURES = [
                                   ctypes.POINTER(c_void_p)]),
     ("smrt_batch_set_stream", c_int, [c_void_p, c_void_p]),
     ("smrt_batch_autotune", c_int, [c_void_p, c_int, ctypes.POINTER(c_int)]),
+    ("smrt_batch_set_shape", c_int, [c_void_p, c_int]),
     ("smrt_batch_step", c_int, [c_void_p, c_longlong]),
     ("smrt_batch_run", c_int, [c_void_p, c_double, c_longlong, c_longlong, c_int, ctypes.POINTER(c_int)]),
     ("smrt_batch_status", c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),

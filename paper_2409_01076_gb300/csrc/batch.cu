@@ -49,8 +49,10 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
-template <int PREC, int KIND, int MODE, int VEC, int BX>
-__global__ void __launch_bounds__(BX, 1024 / BX)   // at most 64 registers: 1024 resident threads per SM
+// CAP bounds the kernel to 64 registers (1024 resident threads per SM); without it the
+// compiler takes what the step needs and fewer blocks are resident.
+template <int PREC, int KIND, int MODE, int VEC, int BX, bool CAP>
+__global__ void __launch_bounds__(BX, CAP ? 1024 / BX : 1)
 batch_step_kernel(const typename Prec<PREC>::R *src, typename Prec<PREC>::R *dst,
                   const BatchCav<typename Prec<PREC>::C> *__restrict__ cav, const int2 *__restrict__ work,
                   const int *__restrict__ counts)
@@ -184,23 +186,32 @@ batch_finish_kernel(const int *__restrict__ act, const int *__restrict__ rpre, c
 
 struct Shape {
     int vec, bx;
+    bool cap;   // 64-register bound
 };
 template <int PREC> struct Shapes;
 template <> struct Shapes<SMRT_PREC_F32> {
-    static constexpr int n = 4;
-    static Shape at(int k) { const Shape s[n] = {{4, 128}, {4, 64}, {4, 256}, {2, 128}}; return s[k]; }
+    static constexpr int n = 5;
+    static Shape at(int k)
+    {
+        const Shape s[n] = {{4, 128, true}, {4, 64, true}, {4, 256, true}, {2, 128, true}, {4, 128, false}};
+        return s[k];
+    }
 };
 template <> struct Shapes<SMRT_PREC_F64> {
-    static constexpr int n = 3;
-    static Shape at(int k) { const Shape s[n] = {{2, 128}, {2, 64}, {1, 128}}; return s[k]; }
+    static constexpr int n = 4;
+    static Shape at(int k)
+    {
+        const Shape s[n] = {{2, 128, true}, {2, 64, true}, {1, 128, true}, {2, 128, false}};
+        return s[k];
+    }
 };
 
-template <int PREC, int KIND, int MODE, int VEC, int BX>
+template <int PREC, int KIND, int MODE, int VEC, int BX, bool CAP = true>
 cudaError_t launch_batch_step_shape(const void *src, void *dst, const void *cav, const int2 *work,
                                     const int *counts, int sms, cudaStream_t s)
 {
     using P = Prec<PREC>;
-    auto kern = batch_step_kernel<PREC, KIND, MODE, VEC, BX>;
+    auto kern = batch_step_kernel<PREC, KIND, MODE, VEC, BX, CAP>;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BX, 0);
     if (e != cudaSuccess) return e;
@@ -220,12 +231,14 @@ cudaError_t launch_batch_step_m(int shape, const void *src, void *dst, const voi
         case 1: return launch_batch_step_shape<PREC, KIND, MODE, 4, 64>(src, dst, cav, work, counts, sms, s);
         case 2: return launch_batch_step_shape<PREC, KIND, MODE, 4, 256>(src, dst, cav, work, counts, sms, s);
         case 3: return launch_batch_step_shape<PREC, KIND, MODE, 2, 128>(src, dst, cav, work, counts, sms, s);
+        case 4: return launch_batch_step_shape<PREC, KIND, MODE, 4, 128, false>(src, dst, cav, work, counts, sms, s);
         }
     } else {
         switch (shape) {
         case 0: return launch_batch_step_shape<PREC, KIND, MODE, 2, 128>(src, dst, cav, work, counts, sms, s);
         case 1: return launch_batch_step_shape<PREC, KIND, MODE, 2, 64>(src, dst, cav, work, counts, sms, s);
         case 2: return launch_batch_step_shape<PREC, KIND, MODE, 1, 128>(src, dst, cav, work, counts, sms, s);
+        case 3: return launch_batch_step_shape<PREC, KIND, MODE, 2, 128, false>(src, dst, cav, work, counts, sms, s);
         }
     }
     return cudaErrorInvalidValue;
@@ -655,6 +668,17 @@ int smrt_batch_set_stream(smrt_batch_t *b, void *stream)
     if (!b) return SMRT_ERR_ARG;
     drop_graph(b);
     b->stream = (cudaStream_t)stream;
+    return SMRT_OK;
+}
+
+int smrt_batch_set_shape(smrt_batch_t *b, int shape)
+{
+    if (!b) return SMRT_ERR_ARG;
+    if (shape < 0 || shape >= nshapes(b->prec))
+        return bfail(b, SMRT_ERR_ARG, "smrt_batch_set_shape: shape %d not in [0, %d)", shape, nshapes(b->prec));
+    drop_graph(b);
+    b->shape = shape;
+    b->list_dirty = true;
     return SMRT_OK;
 }
 

@@ -68,7 +68,7 @@ def test_batch_f32_bitwise_equals_single_lattice_and_autotune_keeps_state(layout
         S.smrt_batch_get_f(b, k, f)
         before.append(f)
     choice = S.smrt_batch_autotune(b, 4)
-    assert 0 <= choice < 4
+    assert 0 <= choice < 5
     steps, _, _ = S.smrt_batch_status(b)
     assert (steps == 13).all()
     for k, (x, y) in enumerate(sizes):
@@ -84,6 +84,36 @@ def test_batch_f32_bitwise_equals_single_lattice_and_autotune_keeps_state(layout
         assert np.array_equal(f, get_f(h)), k
         S.smrt_destroy(h)
     S.smrt_batch_destroy(b)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("layout", [S.SMRT_LAYOUT_AB, S.SMRT_LAYOUT_AA], ids=["ab", "aa"])
+@pytest.mark.parametrize("prec,shapes", [(S.SMRT_PREC_F32, 5), (S.SMRT_PREC_F64, 4)], ids=["f32", "f64"])
+def test_every_tile_shape_matches_single_lattice_bitwise(layout, prec, shapes):
+    """Each autotuner candidate (with and without the register bound) computes the same bits
+    as smrt_step, on lattices narrower and wider than one tile, with ragged rows."""
+    sizes = [(300, 70), (64, 64), (1000, 20), (5, 300), (2, 2), (129, 5)]
+    nx, ny = [s[0] for s in sizes], [s[1] for s in sizes]
+    taus, us = _taus(len(sizes)), _ulids(len(sizes))
+    pname = "f32" if prec == S.SMRT_PREC_F32 else "f64"
+    ref = []
+    for k, (x, y) in enumerate(sizes):
+        h = make(x, y, taus[k], us[k], W.CAVITY, prec=pname, layout="ab" if layout == 0 else "aa")
+        S.smrt_step(h, 11)
+        ref.append(get_f(h))
+        S.smrt_destroy(h)
+    for shape in range(shapes):
+        b = S.smrt_batch_create(nx, ny, taus, us, W.CAVITY, prec, layout)
+        S.smrt_batch_set_shape(b, shape)
+        S.smrt_batch_step(b, 11)
+        for k, (x, y) in enumerate(sizes):
+            f = np.empty((9, y, x))
+            S.smrt_batch_get_f(b, k, f)
+            assert np.array_equal(f, ref[k]), (shape, k)
+        with pytest.raises(S.SmrtError) as ei:
+            S.smrt_batch_set_shape(b, shapes)
+        assert ei.value.status == S.SMRT_ERR_ARG
+        S.smrt_batch_destroy(b)
 
 
 @pytest.mark.gpu
