@@ -47,7 +47,8 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--size", type=int, default=0,
                    help="override the lattice side (profiling on a smaller case of the same workload)")
-    p.add_argument("--report", choices=["", "precision", "batched", "batched-throughput", "learned", "paper"], default="",
+    p.add_argument("--report", choices=["", "precision", "batched", "batched-throughput", "learned", "paper", "unet"],
+                   default="",
                    help="precision: 16-bit vs FP32 storage report; batched: 512 cavities to steady state "
                         "(each prints its own JSON line)")
     p.add_argument("--learned-count", type=int, default=2000)
@@ -57,6 +58,11 @@ def parse_args(argv=None):
     p.add_argument("--batch-count", type=int, default=512)
     p.add_argument("--batch-sides", default="64,128,256,512,1024")
     p.add_argument("--batch-re", default="100,5000", help="Re range (log-uniform) of the batched reports")
+    p.add_argument("--batch-shape", type=int, default=-1,
+                   help="batched-throughput: this tile shape (smrt_batch_set_shape) instead of autotuning")
+    p.add_argument("--unet-batch", type=int, default=16)
+    p.add_argument("--unet-iters", type=int, default=10)
+    p.add_argument("--unet-backend", choices=["both", "tcgen05", "wmma"], default="both")
     p.add_argument("--tol", type=float, default=1e-7)
     p.add_argument("--residual", choices=["stride", "step"], default="stride",
                    help="batched report: stride (mean change per update over a check) or one-step residual")
@@ -497,13 +503,18 @@ def batched_setup(S, count=512, seed=0, layout="ab", sides=(64, 128, 256, 512, 1
     return b, cav
 
 
-def batched_throughput(S, steps, layout="ab", count=512, sides=(64, 128, 256, 512, 1024), re=(100.0, 5000.0)):
+def batched_throughput(S, steps, layout="ab", count=512, sides=(64, 128, 256, 512, 1024), re=(100.0, 5000.0),
+                       shape=-1):
     """MLUPS of smrt_batch_step over the lattices active when the timed call starts (a lattice that
     diverges is still updated until the call returns, and retired after it)."""
     import numpy as np
     import torch
     b, cav = batched_setup(S, count=count, layout=layout, sides=sides, re=re)
-    choice = S.smrt_batch_autotune(b, 10)
+    if shape >= 0:
+        S.smrt_batch_set_shape(b, shape)
+        choice = shape
+    else:
+        choice = S.smrt_batch_autotune(b, 10)
     S.smrt_batch_step(b, 4)
     torch.cuda.synchronize()
     side = np.array([n for n, _ in cav], dtype=np.int64)
@@ -662,6 +673,38 @@ def learned_report(args):
     return 0
 
 
+def unet_report(args):
+    """Training-step time of the warm-start U-Net (32 base channels, 256^2 inputs, seeded synthetic
+    inputs and targets) for each GEMM backend: CUDA events over --unet-iters steps after 3 warm-up steps."""
+    import torch
+    import paper_2409_01076_gb300 as S
+    from paper_2409_01076_gb300.unet import UNet, input_grid
+    torch.cuda.set_device(0)
+    S._lib.load()
+    B = args.unet_batch
+    res = [100.0 * 100.0 ** (k / max(B - 1, 1)) for k in range(B)]
+    x = input_grid(res, 256, 256)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    target = 0.1 * torch.randn((B, 256, 256, 3), device="cuda", generator=g)
+    out = {"report": "unet", "batch": B, "side": 256, "base_channels": 32, "iters": args.unet_iters}
+    for backend in (("tcgen05", "wmma") if args.unet_backend == "both" else (args.unet_backend,)):
+        net = UNet(base=32, gemm=backend)
+        for _ in range(3):
+            net.train_step(x, target, 1e-3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.unet_iters):
+            net.loss_and_grad(x, target)
+            net.adam_step(1e-3)
+        e1.record()
+        torch.cuda.synchronize()
+        out[backend] = {"ms_per_step": round(e0.elapsed_time(e1) / args.unet_iters, 3),
+                        "gemm_timeouts": net.gemm_timeouts(), "params": net.n_params()}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def _oracle_cavity_u(n, re, steps):
     """FP64 oracle: u after `steps` updates of an n x n cavity (U_lid = 0.1) at Reynolds number re."""
     import oracle as O
@@ -746,12 +789,15 @@ def main(argv=None):
         return learned_report(args)
     if args.report == "paper":
         return paper_experiments_report(args)
+    if args.report == "unet":
+        return unet_report(args)
     if args.report == "batched-throughput":
         import torch
         import paper_2409_01076_gb300 as S
         torch.cuda.set_device(0)
         S._lib.load()
-        out = batched_throughput(S, args.steps, args.layout, args.batch_count, _sides(args), _re(args))
+        out = batched_throughput(S, args.steps, args.layout, args.batch_count, _sides(args), _re(args),
+                                 args.batch_shape)
         out["report"] = "batched-throughput"
         print(json.dumps(out), flush=True)
         return 0
