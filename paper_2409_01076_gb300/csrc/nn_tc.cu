@@ -7,8 +7,9 @@
 //      stage in the no-swizzle core-matrix layout: 8 rows x 16 bytes per core matrix
 //      (128 contiguous bytes), core matrices adjacent in K 128 B apart (leading byte
 //      offset), 8-row groups 1024 B apart (stride byte offset).  Rows whose K run is
-//      contiguous in global memory move as 16-byte vectors; transposed operands move as
-//      16-byte vectors along M (or N) scattered into eight core-matrix rows;
+//      contiguous in global memory move as 16-byte vectors; a transposed operand moves as
+//      eight 16-byte vectors along M (or N) per core matrix, transposed in registers into
+//      its eight 16-byte rows.  Each thread issues all its loads before its first store;
 //   2. fence.proxy.async makes those generic-proxy writes visible to the tensor core;
 //   3. thread 0 issues four tcgen05.mma (M 128, N TN, K 16, half x half -> f32) and
 //      commits them to that stage's mbarrier;
@@ -16,7 +17,8 @@
 //      timeout sets *err, waits once more with a limit, and the CTA still releases
 //      its TMEM), so the copy of one stage overlaps the MMAs of the other.
 // Epilogue: warp w reads TMEM lanes 32w..32w+31 (rows of the tile) with tcgen05.ld and
-// writes C, or C^T when trans_c is set.
+// writes C (16-byte stores, or float4 atomics under split-K, when C is 16-byte aligned with
+// ldc % 4 == 0), or C^T when trans_c is set (consecutive lanes write consecutive addresses).
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -74,47 +76,99 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t phase)
     return done != 0;
 }
 
+// Eight halves X[row * ld + k .. + 7] (K-major source), zero past nrows / kend.
+__device__ __forceinline__ uint4 load_k_chunk(const __half *__restrict__ X, int ld, int row, int nrows, int k,
+                                              int kend)
+{
+    if (row >= nrows) return make_uint4(0, 0, 0, 0);
+    if (k + 8 <= kend) return *reinterpret_cast<const uint4 *>(X + (size_t)row * ld + k);
+    __align__(16) __half h[8];
+    #pragma unroll
+    for (int j = 0; j < 8; ++j) h[j] = (k + j < kend) ? X[(size_t)row * ld + k + j] : __float2half(0.0f);
+    return *reinterpret_cast<const uint4 *>(h);
+}
+
+// Eight halves X[k * ld + row .. + 7] (rows contiguous: the source holds op(X)^T), zero past nrows / kend.
+__device__ __forceinline__ uint4 load_mn_chunk(const __half *__restrict__ X, int ld, int k, int kend, int row,
+                                               int nrows)
+{
+    if (k >= kend) return make_uint4(0, 0, 0, 0);
+    if (row + 8 <= nrows) return *reinterpret_cast<const uint4 *>(X + (size_t)k * ld + row);
+    __align__(16) __half h[8];
+    #pragma unroll
+    for (int j = 0; j < 8; ++j) h[j] = (row + j < nrows) ? X[(size_t)k * ld + row + j] : __float2half(0.0f);
+    return *reinterpret_cast<const uint4 *>(h);
+}
+
+template <int W>
+__device__ __forceinline__ uint32_t word(const uint4 &v)
+{
+    return W == 0 ? v.x : W == 1 ? v.y : W == 2 ? v.z : v.w;
+}
+
+// Row R of the transpose of an 8 x 8 block of halves held as in[k] = 8 halves along rows:
+// word w of the result packs (in[2w] half R, in[2w+1] half R).
+template <int R>
+__device__ __forceinline__ uint4 transpose_row(const uint4 in[8])
+{
+    constexpr uint32_t sel = (R & 1) ? 0x7632u : 0x5410u;   // high or low halves of both words
+    uint4 o;
+    o.x = __byte_perm(word<R / 2>(in[0]), word<R / 2>(in[1]), sel);
+    o.y = __byte_perm(word<R / 2>(in[2]), word<R / 2>(in[3]), sel);
+    o.z = __byte_perm(word<R / 2>(in[4]), word<R / 2>(in[5]), sel);
+    o.w = __byte_perm(word<R / 2>(in[6]), word<R / 2>(in[7]), sel);
+    return o;
+}
+
 // Copy rows [r0, r0 + ROWS) x k [k0, k0 + 64) of op(X) into a K-major core-matrix tile.
 // kmajor: X stores each row's K run contiguously (X[row * ld + k]); otherwise X stores
-// op(X)^T (X[k * ld + row]).  vec: 16-byte vectors are allowed (ld % 8 == 0).
+// op(X)^T (X[k * ld + row]).  vec: 16-byte vectors are allowed (ld % 8 == 0, X 16-byte aligned).
+// Every thread issues all of its global loads before its first shared-memory store, so a stage
+// keeps up to eight 16-byte loads per thread in flight.
 template <int ROWS>
 __device__ __forceinline__ void load_tile(__half *tile, const __half *__restrict__ X, int ld, bool kmajor, bool vec,
                                           int r0, int nrows, int k0, int kend)
 {
     const int tid = threadIdx.x;
-    const __half zero = __float2half(0.0f);
-    if (vec) {
-        // ROWS x 8 chunks of 8 halves; a chunk runs along K (kmajor) or along rows (transposed)
-        for (int c = tid; c < ROWS * (TK / 8); c += 128) {
-            if (kmajor) {
-                const int r = c / (TK / 8), kc = (c % (TK / 8)) * 8;
-                const int row = r0 + r, k = k0 + kc;
-                uint4 v = make_uint4(0, 0, 0, 0);
-                if (row < nrows && k + 8 <= kend) {
-                    v = *reinterpret_cast<const uint4 *>(X + (size_t)row * ld + k);
-                } else if (row < nrows) {
-                    __half h[8];
-                    #pragma unroll
-                    for (int j = 0; j < 8; ++j) h[j] = (k + j < kend) ? X[(size_t)row * ld + k + j] : zero;
-                    v = *reinterpret_cast<uint4 *>(h);
-                }
-                *reinterpret_cast<uint4 *>(tile + core_offset(r, kc)) = v;
-            } else {
-                const int kk = c / (ROWS / 8), rc = (c % (ROWS / 8)) * 8;
-                const int row = r0 + rc, k = k0 + kk;
-                __half h[8];
-                if (k < kend && row + 8 <= nrows) {
-                    *reinterpret_cast<uint4 *>(h) = *reinterpret_cast<const uint4 *>(X + (size_t)k * ld + row);
-                } else {
-                    #pragma unroll
-                    for (int j = 0; j < 8; ++j) h[j] = (k < kend && row + j < nrows) ? X[(size_t)k * ld + row + j] : zero;
-                }
-                #pragma unroll
-                for (int j = 0; j < 8; ++j) tile[core_offset(rc + j, kk)] = h[j];
-            }
+    if (vec && kmajor) {
+        constexpr int CH = ROWS * (TK / 8) / 128;     // 16-byte chunks per thread
+        static_assert(CH >= 1 && ROWS * (TK / 8) % 128 == 0, "tile rows");
+        uint4 v[CH];
+        #pragma unroll
+        for (int i = 0; i < CH; ++i) {
+            const int c = tid + i * 128;
+            v[i] = load_k_chunk(X, ld, r0 + c / (TK / 8), nrows, k0 + (c % (TK / 8)) * 8, kend);
+        }
+        #pragma unroll
+        for (int i = 0; i < CH; ++i) {
+            const int c = tid + i * 128;
+            *reinterpret_cast<uint4 *>(tile + core_offset(c / (TK / 8), (c % (TK / 8)) * 8)) = v[i];
         }
         return;
     }
+    if (vec) {
+        // one 8 x 8 core matrix per thread: eight 16-byte loads along the rows (one per k),
+        // transposed in registers into eight 16-byte core-matrix rows
+        static_assert(ROWS <= 128, "one core matrix per thread");
+        if (tid < ROWS) {
+            const int g = tid % (ROWS / 8), kg = tid / (ROWS / 8);
+            const int row = r0 + g * 8, kb = k0 + kg * 8;
+            uint4 in[8];
+            #pragma unroll
+            for (int j = 0; j < 8; ++j) in[j] = load_mn_chunk(X, ld, kb + j, kend, row, nrows);
+            __half *dst = tile + core_offset(g * 8, kg * 8);   // rows g*8 .. g*8+7 are 8 halves apart
+            *reinterpret_cast<uint4 *>(dst + 0 * 8) = transpose_row<0>(in);
+            *reinterpret_cast<uint4 *>(dst + 1 * 8) = transpose_row<1>(in);
+            *reinterpret_cast<uint4 *>(dst + 2 * 8) = transpose_row<2>(in);
+            *reinterpret_cast<uint4 *>(dst + 3 * 8) = transpose_row<3>(in);
+            *reinterpret_cast<uint4 *>(dst + 4 * 8) = transpose_row<4>(in);
+            *reinterpret_cast<uint4 *>(dst + 5 * 8) = transpose_row<5>(in);
+            *reinterpret_cast<uint4 *>(dst + 6 * 8) = transpose_row<6>(in);
+            *reinterpret_cast<uint4 *>(dst + 7 * 8) = transpose_row<7>(in);
+        }
+        return;
+    }
+    const __half zero = __float2half(0.0f);
     for (int idx = tid; idx < ROWS * TK; idx += 128) {
         int r, kk;
         if (kmajor) { r = idx / TK; kk = idx % TK; }
@@ -130,7 +184,7 @@ template <int TN>
 __global__ void __launch_bounds__(128)
 gemm_tc_kernel(int transA, int transB, int M, int N, int K, float alpha, const __half *__restrict__ A, int lda,
                const __half *__restrict__ B, int ldb, float beta, float *C, int ldc, int trans_c, int k_chunk,
-               int atomic, int vec_a, int vec_b, int *err)
+               int atomic, int vec_a, int vec_b, int vec_c, int *err)
 {
     constexpr uint32_t kCols = TN;          // TMEM columns: one f32 column per output column
     // dynamic shared memory: two stages of A (128 x 64) then two of B (TN x 64), 1024-byte aligned
@@ -226,7 +280,27 @@ gemm_tc_kernel(int transA, int transB, int M, int N, int K, float alpha, const _
                            "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
                          : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (row < M) {
+            if (row < M && !trans_c && vec_c && n0 + c + 32 <= N) {
+                // 32 consecutive columns of this thread's row: eight 16-byte stores (or float4 atomics)
+                float *crow = C + (size_t)row * ldc + n0 + c;
+                #pragma unroll
+                for (int j = 0; j < 32; j += 4) {
+                    float4 v = any ? make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                                 __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]))
+                                   : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    v.x *= alpha; v.y *= alpha; v.z *= alpha; v.w *= alpha;
+                    float4 *cp = reinterpret_cast<float4 *>(crow + j);
+                    if (atomic) {
+                        atomicAdd(cp, v);
+                    } else {
+                        if (beta != 0.0f) {
+                            const float4 o = *cp;
+                            v.x += beta * o.x; v.y += beta * o.y; v.z += beta * o.z; v.w += beta * o.w;
+                        }
+                        *cp = v;
+                    }
+                }
+            } else if (row < M) {
                 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int n = n0 + c + j;
@@ -266,6 +340,7 @@ cudaError_t launch_tc(int transA, int transB, int M, int N, int K, float alpha, 
     if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
     const int aligned_a = (lda % 8 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
     const int aligned_b = (ldb % 8 == 0) && ((reinterpret_cast<uintptr_t>(B) & 15) == 0);
+    const int aligned_c = (ldc % 4 == 0) && ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
     const size_t smem = 2 * (size_t)(TM + TN) * TK * sizeof(__half);
     static bool attr_set = false;       // per instantiation; the attribute is per function
     if (!attr_set) {
@@ -276,7 +351,7 @@ cudaError_t launch_tc(int transA, int transB, int M, int N, int K, float alpha, 
     }
     gemm_tc_kernel<TN><<<grid, 128, smem, s>>>(transA, transB, M, N, K, alpha, (const __half *)A, lda,
                                             (const __half *)B, ldb, beta, C, ldc, trans_c, chunk,
-                                            split_k > 1 ? 1 : 0, aligned_a, aligned_b, err);
+                                            split_k > 1 ? 1 : 0, aligned_a, aligned_b, aligned_c, err);
     return cudaGetLastError();
 }
 

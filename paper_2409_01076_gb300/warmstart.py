@@ -65,8 +65,11 @@ def generate_dataset(res, n: int = 256, tol: float = 1e-7, check_every: int = 10
 
 
 def train(net, res, targets, iters: int = 2000, batch: int = 16, lr: float = 2e-3, seed: int = 0,
-          log_every: int = 100):
-    """Adam on random mini-batches with a cosine learning-rate decay; returns the loss history."""
+          log_every: int = 100, warmup: int = 100):
+    """Adam on random mini-batches: the learning rate rises linearly over the first `warmup`
+    iterations, under a cosine decay over all of them.  (Without the warm-up, Adam's first steps
+    move every weight by about lr, whatever the size of its gradient, and the run-to-run spread
+    of the final loss grows several-fold.)  Returns the loss history and the seconds taken."""
     import torch
     from .unet import input_grid
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -78,7 +81,7 @@ def train(net, res, targets, iters: int = 2000, batch: int = 16, lr: float = 2e-
         idx = rng.choice(count, size=min(batch, count), replace=False)
         x = input_grid([res[i] for i in idx], n, n)
         tgt = targets[torch.as_tensor(idx, device=targets.device)].contiguous()
-        cur = lr * 0.5 * (1.0 + math.cos(math.pi * it / iters))
+        cur = lr * min(1.0, (it + 1) / max(warmup, 1)) * 0.5 * (1.0 + math.cos(math.pi * it / iters))
         loss = net.train_step(x, tgt, cur)
         if it % log_every == 0 or it == iters - 1:
             hist.append((it, loss))
