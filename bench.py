@@ -312,6 +312,25 @@ def oracle_sample(wl, side, steps):
     return side * side * steps / sec / 1e6, sec
 
 
+def cpu_model():
+    """The host CPU as /proc/cpuinfo names it (x86 'model name'; Arm implementer and part codes)."""
+    import platform
+    fields = {}
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    fields.setdefault(k.strip(), v.strip())
+    except OSError:
+        pass
+    if "model name" in fields:
+        return fields["model name"]
+    if "CPU part" in fields:
+        return "%s implementer %s part %s" % (platform.machine(), fields.get("CPU implementer", "?"), fields["CPU part"])
+    return platform.machine() or "unknown"
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -365,7 +384,7 @@ def cpu_baseline(wl, budget_s=8.0):
     finally:
         pool.terminate()
     return {"value": round(mlups, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
-            "single_core_value": round(mlups1, 3),
+            "single_core_value": round(mlups1, 3), "cpu": cpu_model(),
             "sample": "%dx%d window of the same workload (%s), %d steps, FP64 C oracle: one process per host "
                       "core (%d), each on its own window, %.1f s wall; single-threaded %.1f s"
                       % (side, side, wl["name"], steps, cores, sec, sec1)}
@@ -399,7 +418,7 @@ def reference_arm(args):
         "config": {"workload": wl["desc"], "sample": "%dx%d window per core per step" % (side, side),
                    "l2": "CPU run; no GPU L2 involved"},
         "cpu_baseline": {"value": round(mlups, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
-                         "sample": "%dx%d window of %s per core, one update per step, FP64 C oracle in one "
+                         "cpu": cpu_model(), "sample": "%dx%d window of %s per core, one update per step, FP64 C oracle in one "
                                    "process per host core" % (side, side, wl["name"])},
         "e2e": {"value": round(mlups, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -651,8 +670,9 @@ def learned_report(args):
     out["dataset"] = info
     net = UNet(base=32, seed=0)
     out["params"] = net.n_params()
-    hist, train_s = WS.train(net, res_train, targets, iters=args.learned_iters, batch=16, lr=2e-3)
-    out["training"] = {"iters": args.learned_iters, "batch": 16, "seconds": round(train_s, 2),
+    hist, train_s = WS.train(net, res_train, targets, iters=args.learned_iters, batch=16, lr=1e-3, warmup=100)
+    out["training"] = {"iters": args.learned_iters, "batch": 16, "lr": 1e-3, "warmup": 100,
+                       "seconds": round(train_s, 2),
                        "loss_first_last": [hist[0][1], hist[-1][1]], "loss_history": hist[::4],
                        "final_loss_scale": net.grad_scale}
     del targets

@@ -47,9 +47,21 @@ SMRT_API int smrt_nn_gemm_tc(int transA, int transB, int M, int N, int K, float 
                              const void *B, int ldb, float beta, float *C, int ldc, int split_k, int *err,
                              void *stream);
 
-/* 3x3, stride 1, zero padding 1 patches of x (N,H,W,C float32) into
- * col (N*H*W rows x 9*C half, row-major): col[p][(ky*3+kx)*C + c] = x[n][y+ky-1][x+kx-1][c]. */
-SMRT_API int smrt_nn_im2col3(const float *x, int N, int H, int W, int C, void *col, void *stream);
+/* 3x3, stride 1, zero padding 1 convolution as an implicit GEMM on the tensor cores:
+ *   y[p][o] = alpha * sum_{tap, c} half(x[n][yy+ky-1][xx+kx-1][c]) * w[o][tap*C + c] + beta * y[p][o]
+ * for pixel p = (n*H + yy)*W + xx, tap = ky*3 + kx, outside the image x = 0.  x is NHWC float32
+ * (C % 8 == 0, 16-byte aligned), w is cout x 9C half (row-major, the layout of smrt_nn_im2col3's
+ * columns), y is N*H*W rows of ldy >= cout float32.  The result is bit-identical to smrt_nn_im2col3
+ * followed by smrt_nn_gemm_tc(0, 1, ...): the kernel is that GEMM, with each A tile gathered from x
+ * (rounded to half as im2col rounds) instead of read from an im2col matrix, which is never built.
+ * err as in smrt_nn_gemm_tc.  SMRT_ERR_ARG for C % 8 != 0, a misaligned x or bad sizes. */
+SMRT_API int smrt_nn_conv3_tc(const float *x, int N, int H, int W, int C, const void *w, int cout, float alpha,
+                              float beta, float *y, int ldy, int *err, void *stream);
+
+/* 3x3, stride 1, zero padding 1 patches of x (N,H,W,C float32) into col (N*H*W rows of
+ * ld >= 9*C halves, row-major): col[p*ld + (ky*3+kx)*C + c] = x[n][y+ky-1][x+kx-1][c].
+ * Columns 9*C .. ld-1 are set to zero (a padded ld lets a GEMM read whole 16-byte rows). */
+SMRT_API int smrt_nn_im2col3(const float *x, int N, int H, int W, int C, void *col, int ld, void *stream);
 
 /* Adjoint of smrt_nn_im2col3: dx[n][y][x][c] = sum over the 9 patches that read it of dcol (float32). */
 SMRT_API int smrt_nn_col2im3(const float *dcol, int N, int H, int W, int C, float *dx, void *stream);
@@ -61,6 +73,11 @@ SMRT_API int smrt_nn_flip3(const float *w, int cout, int cin, void *wf, void *st
 
 /* dst[i] = (half)(scale * src[i]), n elements. */
 SMRT_API int smrt_nn_to_half(const float *src, long long n, float scale, void *dst, void *stream);
+
+/* Row-padded conversion: src is rows x cols float32 (dense), dst rows x ld halves with
+ * dst[r*ld + c] = (half)(scale * src[r*cols + c]) for c < cols and 0 for cols <= c < ld. */
+SMRT_API int smrt_nn_to_half_rows(const float *src, long long rows, int cols, float scale, void *dst, int ld,
+                                  void *stream);
 
 /* z = x + bias[c] (x, z: rows x C), then a = SiLU(z) = z / (1 + exp(-z)) if act, else a = z.
  * z may be NULL (not kept); a may alias x. */

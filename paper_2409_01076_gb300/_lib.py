@@ -56,10 +56,13 @@ SIGNATURES = [
                              ctypes.c_float, c_void_p, c_int, c_int, c_void_p]),
     ("smrt_nn_gemm_tc", c_int, [c_int, c_int, c_int, c_int, c_int, ctypes.c_float, c_void_p, c_int, c_void_p, c_int,
                                 ctypes.c_float, c_void_p, c_int, c_int, c_void_p, c_void_p]),
-    ("smrt_nn_im2col3", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p]),
+    ("smrt_nn_conv3_tc", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_int, ctypes.c_float,
+                                 ctypes.c_float, c_void_p, c_int, c_void_p, c_void_p]),
+    ("smrt_nn_im2col3", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_int, c_void_p]),
     ("smrt_nn_col2im3", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p]),
     ("smrt_nn_flip3", c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p]),
     ("smrt_nn_to_half", c_int, [c_void_p, c_longlong, ctypes.c_float, c_void_p, c_void_p]),
+    ("smrt_nn_to_half_rows", c_int, [c_void_p, c_longlong, c_int, ctypes.c_float, c_void_p, c_int, c_void_p]),
     ("smrt_nn_bias_act", c_int, [c_void_p, c_void_p, c_longlong, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     ("smrt_nn_bias_act_bwd", c_int, [c_void_p, c_void_p, c_longlong, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     ("smrt_nn_avgpool2", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p]),

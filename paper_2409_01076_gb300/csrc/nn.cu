@@ -94,26 +94,29 @@ gemm_kernel(int transA, int transB, int M, int N, int K, float alpha, const __ha
     }
 }
 
-__global__ void im2col3_kernel(const float *__restrict__ x, int N, int H, int W, int C, __half *__restrict__ col)
+__global__ void im2col3_kernel(const float *__restrict__ x, int N, int H, int W, int C, __half *__restrict__ col,
+                               int ld)
 {
-    const long long total = (long long)N * H * W * 9 * C;
+    const long long total = (long long)N * H * W * ld;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(t % C);
-        long long r = t / C;
-        const int tap = (int)(r % 9);
-        const long long p = r / 9;
-        const int xx = (int)(p % W), yy = (int)((p / W) % H), n = (int)(p / ((long long)W * H));
-        const int sy = yy + tap / 3 - 1, sx = xx + tap % 3 - 1;
-        float v = 0.0f;
-        if (sy >= 0 && sy < H && sx >= 0 && sx < W) v = x[(((size_t)n * H + sy) * W + sx) * C + c];
+        const int j = (int)(t % ld);
+        const long long p = t / ld;
+        float v = 0.0f;                 // the pad columns 9C .. ld-1 stay zero
+        if (j < 9 * C) {
+            const int tap = j / C, c = j % C;
+            const int xx = (int)(p % W), yy = (int)((p / W) % H), n = (int)(p / ((long long)W * H));
+            const int sy = yy + tap / 3 - 1, sx = xx + tap % 3 - 1;
+            if (sy >= 0 && sy < H && sx >= 0 && sx < W) v = x[(((size_t)n * H + sy) * W + sx) * C + c];
+        }
         col[t] = __float2half(v);
     }
 }
 
-// C % 8 == 0: one thread per (pixel, tap, 8-channel chunk), two float4 loads, one 16-byte store.
-// Requires N*H*W*9*(C/8) < 2^31.
-__global__ void im2col3_vec_kernel(const float *__restrict__ x, int N, int H, int W, int C, __half *__restrict__ col)
+// C % 8 == 0 and ld == 9 C: one thread per (pixel, tap, 8-channel chunk), two float4 loads, one
+// 16-byte store.  Requires N*H*W*9*(C/8) < 2^31.
+__global__ void im2col3_vec_kernel(const float *__restrict__ x, int N, int H, int W, int C, __half *__restrict__ col,
+                                   int ld)
 {
     const int cc = C >> 3;
     const int total = N * H * W * 9 * cc;
@@ -136,7 +139,7 @@ __global__ void im2col3_vec_kernel(const float *__restrict__ x, int N, int H, in
             out.z = *reinterpret_cast<unsigned *>(&h2);
             out.w = *reinterpret_cast<unsigned *>(&h3);
         }
-        reinterpret_cast<uint4 *>(col)[(size_t)p * 9 * cc + (size_t)tap * cc + chunk] = out;
+        reinterpret_cast<uint4 *>(col)[(size_t)p * (ld >> 3) + (size_t)tap * cc + chunk] = out;
     }
 }
 
@@ -175,6 +178,18 @@ __global__ void to_half_kernel(const float *__restrict__ s, long long n, float s
 {
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
         d[t] = __float2half(scale * s[t]);
+}
+
+// Rows of `cols` floats into rows of `ld` halves, the pad columns zeroed.
+__global__ void to_half_rows_kernel(const float *__restrict__ s, long long rows, int cols, float scale,
+                                    __half *__restrict__ d, int ld)
+{
+    const long long n = rows * ld;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const long long r = t / ld;
+        const int c = (int)(t % ld);
+        d[t] = c < cols ? __float2half(scale * s[r * cols + c]) : __float2half(0.0f);
+    }
 }
 
 __device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + expf(-z)); }
@@ -412,16 +427,18 @@ int smrt_nn_gemm(int transA, int transB, int M, int N, int K, float alpha, const
     return launched("smrt_nn_gemm");
 }
 
-int smrt_nn_im2col3(const float *x, int N, int H, int W, int C, void *col, void *stream)
+int smrt_nn_im2col3(const float *x, int N, int H, int W, int C, void *col, int ld, void *stream)
 {
-    if (!x || !col || N < 1 || H < 1 || W < 1 || C < 1) return nn_fail(SMRT_ERR_ARG, "smrt_nn_im2col3: bad arguments");
+    if (!x || !col || N < 1 || H < 1 || W < 1 || C < 1 || ld < 9 * C)
+        return nn_fail(SMRT_ERR_ARG, "smrt_nn_im2col3: bad arguments");
     const long long chunks = (long long)N * H * W * 9 * (C / 8);
-    if (C % 8 == 0 && chunks < (1LL << 31) && ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(col)) & 15) == 0) {
-        im2col3_vec_kernel<<<grid_for(chunks), 256, 0, (cudaStream_t)stream>>>(x, N, H, W, C, (__half *)col);
+    if (C % 8 == 0 && ld == 9 * C && chunks < (1LL << 31) &&
+        ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(col)) & 15) == 0) {
+        im2col3_vec_kernel<<<grid_for(chunks), 256, 0, (cudaStream_t)stream>>>(x, N, H, W, C, (__half *)col, ld);
         return launched("smrt_nn_im2col3");
     }
-    im2col3_kernel<<<grid_for((long long)N * H * W * 9 * C), 256, 0, (cudaStream_t)stream>>>(x, N, H, W, C,
-                                                                                             (__half *)col);
+    im2col3_kernel<<<grid_for((long long)N * H * W * ld), 256, 0, (cudaStream_t)stream>>>(x, N, H, W, C,
+                                                                                          (__half *)col, ld);
     return launched("smrt_nn_im2col3");
 }
 
@@ -437,6 +454,14 @@ int smrt_nn_flip3(const float *w, int cout, int cin, void *wf, void *stream)
     if (!w || !wf || cout < 1 || cin < 1) return nn_fail(SMRT_ERR_ARG, "smrt_nn_flip3: bad arguments");
     flip3_kernel<<<grid_for((long long)cout * 9 * cin), 256, 0, (cudaStream_t)stream>>>(w, cout, cin, (__half *)wf);
     return launched("smrt_nn_flip3");
+}
+
+int smrt_nn_to_half_rows(const float *src, long long rows, int cols, float scale, void *dst, int ld, void *stream)
+{
+    if (!src || !dst || rows < 0 || cols < 1 || ld < cols) return nn_fail(SMRT_ERR_ARG, "smrt_nn_to_half_rows: bad arguments");
+    if (rows == 0) return SMRT_OK;
+    to_half_rows_kernel<<<grid_for(rows * ld), 256, 0, (cudaStream_t)stream>>>(src, rows, cols, scale, (__half *)dst, ld);
+    return launched("smrt_nn_to_half_rows");
 }
 
 int smrt_nn_to_half(const float *src, long long n, float scale, void *dst, void *stream)

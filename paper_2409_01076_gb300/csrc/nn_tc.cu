@@ -1,12 +1,13 @@
-// nn_tc.cu -- smrt_nn_gemm_tc: the GEMM of include/smrt_nn.h on the 5th-generation
-// tensor cores (tcgen05): operands staged in shared memory, accumulator in TMEM.
+// nn_tc.cu -- smrt_nn_gemm_tc (the GEMM of include/smrt_nn.h) and smrt_nn_conv3_tc (the same
+// kernel with its A operand gathered as an implicit im2col of a 3x3 convolution) on the
+// 5th-generation tensor cores (tcgen05): operands staged in shared memory, accumulator in TMEM.
 //
 // One 128-thread CTA computes a 128 x TN tile of C (TN = 32, 64 or 128, picked from N).
 // Per K step of 64, double-buffered over two shared-memory stages:
 //   1. all threads copy op(A)[128 x 64] and op(B)^T[TN x 64] (both K-major) into one
 //      stage in the no-swizzle core-matrix layout: 8 rows x 16 bytes per core matrix
 //      (128 contiguous bytes), core matrices adjacent in K 128 B apart (leading byte
-//      offset), 8-row groups 1024 B apart (stride byte offset).  Rows whose K run is
+//      offset), 8-row groups 1040 B apart (stride byte offset: 1024 plus a 16-byte bank skew).  Rows whose K run is
 //      contiguous in global memory move as 16-byte vectors; a transposed operand moves as
 //      eight 16-byte vectors along M (or N) per core matrix, transposed in registers into
 //      its eight 16-byte rows.  Each thread issues all its loads before its first store;
@@ -39,10 +40,19 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p)
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
+// 8-row groups of a tile lie kGroupBytes apart: the 1024 bytes of their eight K-adjacent core
+// matrices plus a 16-byte skew, so that the groups' core matrices start in different shared
+// memory banks (a warp that writes one core-matrix row per thread into 8 groups is conflict-free).
+constexpr int kGroupBytes = (TK / 8) * 128 + 16;
+constexpr int kGroupHalves = kGroupBytes / 2;
+
+template <int ROWS>
+constexpr int tile_halves() { return (ROWS / 8) * kGroupHalves; }
+
 // Offset (in halves) of element (row, k) of a rows x 64 K-major tile in the core-matrix layout.
 __device__ __forceinline__ int core_offset(int row, int k)
 {
-    return ((row >> 3) * (TK / 8) + (k >> 3)) * 64 + (row & 7) * 8 + (k & 7);
+    return (row >> 3) * kGroupHalves + (k >> 3) * 64 + (row & 7) * 8 + (k & 7);
 }
 
 // Shared-memory matrix descriptor: start address, leading byte offset (between core
@@ -133,16 +143,20 @@ __device__ __forceinline__ void load_tile(__half *tile, const __half *__restrict
     if (vec && kmajor) {
         constexpr int CH = ROWS * (TK / 8) / 128;     // 16-byte chunks per thread
         static_assert(CH >= 1 && ROWS * (TK / 8) % 128 == 0, "tile rows");
+        // chunk c: row (c / 64) * 8 + c % 8, K offset ((c / 8) % 8) * 8 -- the rows of one core
+        // matrix go to consecutive lanes, so a warp's 16-byte stores cover all banks
         uint4 v[CH];
         #pragma unroll
         for (int i = 0; i < CH; ++i) {
             const int c = tid + i * 128;
-            v[i] = load_k_chunk(X, ld, r0 + c / (TK / 8), nrows, k0 + (c % (TK / 8)) * 8, kend);
+            const int r = (c >> 6) * 8 + (c & 7), kc = ((c >> 3) & 7) * 8;
+            v[i] = load_k_chunk(X, ld, r0 + r, nrows, k0 + kc, kend);
         }
         #pragma unroll
         for (int i = 0; i < CH; ++i) {
             const int c = tid + i * 128;
-            *reinterpret_cast<uint4 *>(tile + core_offset(c / (TK / 8), (c % (TK / 8)) * 8)) = v[i];
+            const int r = (c >> 6) * 8 + (c & 7), kc = ((c >> 3) & 7) * 8;
+            *reinterpret_cast<uint4 *>(tile + core_offset(r, kc)) = v[i];
         }
         return;
     }
@@ -180,17 +194,55 @@ __device__ __forceinline__ void load_tile(__half *tile, const __half *__restrict
     }
 }
 
-template <int TN>
+// Source of the implicit im2col operand of a 3x3, stride-1, zero-padding-1 convolution:
+// x is NHWC float32 with C % 8 == 0, 16-byte aligned.
+struct ConvSrc {
+    const float *x;
+    int H, W, C;
+};
+
+// Row t of the A tile (t = threadIdx.x, pixel (n, yy, xx)), K positions [k0, k0 + 64) of the
+// implicit im2col matrix: K index (ky*3 + kx)*C + c reads x[n][yy+ky-1][xx+kx-1][c], zero outside
+// the image, at k >= kend or for a row past the last pixel.  Eight 8-channel chunks, all loads
+// issued before the stores; the rows of a core matrix go to consecutive lanes.  The halves are
+// rounded exactly as smrt_nn_im2col3 rounds them.
+__device__ __forceinline__ void load_conv_tile(__half *tile, const ConvSrc &cs, int n, int yy, int xx, bool valid,
+                                               int k0, int kend)
+{
+    int tap = k0 / cs.C, c = k0 - tap * cs.C;
+    uint4 v[TK / 8];
+    #pragma unroll
+    for (int j = 0; j < TK / 8; ++j) {
+        v[j] = make_uint4(0, 0, 0, 0);
+        const int sy = yy + tap / 3 - 1, sx = xx + tap % 3 - 1;
+        if (valid && k0 + 8 * j < kend && sy >= 0 && sy < cs.H && sx >= 0 && sx < cs.W) {
+            const float4 *src = reinterpret_cast<const float4 *>(cs.x + (((size_t)n * cs.H + sy) * cs.W + sx) * cs.C + c);
+            const float4 a = src[0], b = src[1];
+            __half2 h0 = __floats2half2_rn(a.x, a.y), h1 = __floats2half2_rn(a.z, a.w);
+            __half2 h2 = __floats2half2_rn(b.x, b.y), h3 = __floats2half2_rn(b.z, b.w);
+            v[j] = make_uint4(*reinterpret_cast<uint32_t *>(&h0), *reinterpret_cast<uint32_t *>(&h1),
+                              *reinterpret_cast<uint32_t *>(&h2), *reinterpret_cast<uint32_t *>(&h3));
+        }
+        c += 8;
+        if (c >= cs.C) { c -= cs.C; ++tap; }
+    }
+    #pragma unroll
+    for (int j = 0; j < TK / 8; ++j)
+        *reinterpret_cast<uint4 *>(tile + core_offset(threadIdx.x, 8 * j)) = v[j];
+}
+
+template <int TN, bool CONV>
 __global__ void __launch_bounds__(128)
 gemm_tc_kernel(int transA, int transB, int M, int N, int K, float alpha, const __half *__restrict__ A, int lda,
                const __half *__restrict__ B, int ldb, float beta, float *C, int ldc, int trans_c, int k_chunk,
-               int atomic, int vec_a, int vec_b, int vec_c, int *err)
+               int atomic, int vec_a, int vec_b, int vec_c, ConvSrc cs, int *err)
 {
     constexpr uint32_t kCols = TN;          // TMEM columns: one f32 column per output column
     // dynamic shared memory: two stages of A (128 x 64) then two of B (TN x 64), 1024-byte aligned
     extern __shared__ __align__(1024) unsigned char dyn[];
-    __half(*sA)[TM * TK] = reinterpret_cast<__half(*)[TM * TK]>(dyn);
-    __half(*sB)[TN * TK] = reinterpret_cast<__half(*)[TN * TK]>(dyn + 2 * TM * TK * sizeof(__half));
+    __half(*sA)[tile_halves<TM>()] = reinterpret_cast<__half(*)[tile_halves<TM>()]>(dyn);
+    __half(*sB)[tile_halves<TN>()] =
+        reinterpret_cast<__half(*)[tile_halves<TN>()]>(dyn + 2 * tile_halves<TM>() * sizeof(__half));
     __shared__ __align__(8) unsigned long long mbar[2];
     __shared__ uint32_t tmem_holder;
     __shared__ int failed;
@@ -215,6 +267,17 @@ gemm_tc_kernel(int transA, int transB, int M, int N, int K, float alpha, const _
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_holder;
 
+    // CONV: this thread's output pixel (row m0 + tid of the implicit im2col matrix)
+    int pn = 0, py = 0, px = 0;
+    const bool pvalid = m0 + tid < M;
+    if (CONV && pvalid) {
+        const int p = m0 + tid, hw = cs.H * cs.W;
+        pn = p / hw;
+        const int rem = p - pn * hw;
+        py = rem / cs.W;
+        px = rem - py * cs.W;
+    }
+
     uint32_t phase[2] = {0u, 0u};
     bool pending[2] = {false, false};
     int step = 0;
@@ -229,7 +292,8 @@ gemm_tc_kernel(int transA, int transB, int M, int N, int K, float alpha, const _
             phase[s] ^= 1u;
             pending[s] = false;
         }
-        load_tile<TM>(sA[s], A, lda, !transA, vec_a, m0, M, k0, kend);
+        if constexpr (CONV) load_conv_tile(sA[s], cs, pn, py, px, pvalid, k0, kend);
+        else load_tile<TM>(sA[s], A, lda, !transA, vec_a, m0, M, k0, kend);
         load_tile<TN>(sB[s], B, ldb, transB, vec_b, n0, N, k0, kend);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
@@ -239,8 +303,8 @@ gemm_tc_kernel(int transA, int transB, int M, int N, int K, float alpha, const _
             const uint32_t sa = smem_addr(sA[s]), sb = smem_addr(sB[s]);
             #pragma unroll
             for (int kk = 0; kk < TK / 16; ++kk) {
-                const unsigned long long ad = make_desc(sa + kk * 256, 128, (TK / 8) * 128);
-                const unsigned long long bd = make_desc(sb + kk * 256, 128, (TK / 8) * 128);
+                const unsigned long long ad = make_desc(sa + kk * 256, 128, kGroupBytes);
+                const unsigned long long bd = make_desc(sb + kk * 256, 128, kGroupBytes);
                 const uint32_t acc = (step > 0 || kk > 0) ? 1u : 0u;
                 asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
@@ -329,9 +393,10 @@ int tc_fail(int code, const char *fmt, ...)
     return code;
 }
 
-template <int TN>
+template <int TN, bool CONV = false>
 cudaError_t launch_tc(int transA, int transB, int M, int N, int K, float alpha, const void *A, int lda, const void *B,
-                      int ldb, float beta, float *C, int ldc, int trans_c, int split_k, int *err, cudaStream_t s)
+                      int ldb, float beta, float *C, int ldc, int trans_c, int split_k, int *err, cudaStream_t s,
+                      ConvSrc cs = ConvSrc{nullptr, 0, 0, 0})
 {
     int chunk = (K + split_k - 1) / split_k;
     chunk = ((chunk + TK - 1) / TK) * TK;
@@ -341,17 +406,17 @@ cudaError_t launch_tc(int transA, int transB, int M, int N, int K, float alpha, 
     const int aligned_a = (lda % 8 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
     const int aligned_b = (ldb % 8 == 0) && ((reinterpret_cast<uintptr_t>(B) & 15) == 0);
     const int aligned_c = (ldc % 4 == 0) && ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
-    const size_t smem = 2 * (size_t)(TM + TN) * TK * sizeof(__half);
+    const size_t smem = 2 * (size_t)(tile_halves<TM>() + tile_halves<TN>()) * sizeof(__half);
     static bool attr_set = false;       // per instantiation; the attribute is per function
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<TN, CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    gemm_tc_kernel<TN><<<grid, 128, smem, s>>>(transA, transB, M, N, K, alpha, (const __half *)A, lda,
-                                            (const __half *)B, ldb, beta, C, ldc, trans_c, chunk,
-                                            split_k > 1 ? 1 : 0, aligned_a, aligned_b, aligned_c, err);
+    gemm_tc_kernel<TN, CONV><<<grid, 128, smem, s>>>(transA, transB, M, N, K, alpha, (const __half *)A, lda,
+                                                  (const __half *)B, ldb, beta, C, ldc, trans_c, chunk,
+                                                  split_k > 1 ? 1 : 0, aligned_a, aligned_b, aligned_c, cs, err);
     return cudaGetLastError();
 }
 
@@ -375,5 +440,24 @@ extern "C" int smrt_nn_gemm_tc(int transA, int transB, int M, int N, int K, floa
     else if (N <= 64) e = launch_tc<64>(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, trans_c, split_k, err, s);
     else e = launch_tc<128>(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, trans_c, split_k, err, s);
     if (e != cudaSuccess) return tc_fail(SMRT_ERR_CUDA, "smrt_nn_gemm_tc: %s", cudaGetErrorString(e));
+    return SMRT_OK;
+}
+
+extern "C" int smrt_nn_conv3_tc(const float *x, int N, int H, int W, int C, const void *w, int cout, float alpha,
+                                float beta, float *y, int ldy, int *err, void *stream)
+{
+    const long long rows = (long long)N * H * W;
+    if (!x || !w || !y || N < 1 || H < 1 || W < 1 || C < 8 || C % 8 != 0 || cout < 1 || ldy < cout ||
+        (reinterpret_cast<uintptr_t>(x) & 15) != 0 || rows > 0x7fffffffLL || 9LL * C > 0x7fffffffLL)
+        return tc_fail(SMRT_ERR_ARG, "smrt_nn_conv3_tc: bad arguments (N %d H %d W %d C %d cout %d ldy %d)", N, H, W,
+                       C, cout, ldy);
+    const int M = (int)rows, K = 9 * C;
+    const ConvSrc cs{x, H, W, C};
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if (cout <= 32) e = launch_tc<32, true>(0, 1, M, cout, K, alpha, nullptr, K, w, K, beta, y, ldy, 0, 1, err, s, cs);
+    else if (cout <= 64) e = launch_tc<64, true>(0, 1, M, cout, K, alpha, nullptr, K, w, K, beta, y, ldy, 0, 1, err, s, cs);
+    else e = launch_tc<128, true>(0, 1, M, cout, K, alpha, nullptr, K, w, K, beta, y, ldy, 0, 1, err, s, cs);
+    if (e != cudaSuccess) return tc_fail(SMRT_ERR_CUDA, "smrt_nn_conv3_tc: %s", cudaGetErrorString(e));
     return SMRT_OK;
 }

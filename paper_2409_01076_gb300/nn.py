@@ -36,9 +36,18 @@ def smrt_nn_gemm_tc(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc
                                        _p(err), _s()))
 
 
+def smrt_nn_conv3_tc(x, w, y, alpha=1.0, beta=0.0, err=None):
+    """x: (N, H, W, C) float32; w: (cout, 9C) half; y: N*H*W rows of cout float32 (any view)."""
+    n, h, wd, c = x.shape
+    cout = w.shape[0]
+    _check(_lib.load().smrt_nn_conv3_tc(_p(x), n, h, wd, c, _p(w), int(cout), float(alpha), float(beta), _p(y),
+                                        int(y.shape[-1]), _p(err), _s()))
+
+
 def smrt_nn_im2col3(x, col):
+    """col: (N*H*W, ld) half with ld >= 9*C (the row stride is taken from col)."""
     n, h, w, c = x.shape
-    _check(_lib.load().smrt_nn_im2col3(_p(x), n, h, w, c, _p(col), _s()))
+    _check(_lib.load().smrt_nn_im2col3(_p(x), n, h, w, c, _p(col), int(col.shape[-1]), _s()))
 
 
 def smrt_nn_col2im3(dcol, shape, dx):
@@ -53,6 +62,13 @@ def smrt_nn_flip3(w, wf):
 
 def smrt_nn_to_half(src, dst, scale=1.0):
     _check(_lib.load().smrt_nn_to_half(_p(src), src.numel(), float(scale), _p(dst), _s()))
+
+
+def smrt_nn_to_half_rows(src, dst, scale=1.0):
+    """src: (rows, cols) float32; dst: (rows, ld) half, ld >= cols, pad columns zeroed."""
+    rows, cols = src.shape[0], src.numel() // max(src.shape[0], 1)
+    _check(_lib.load().smrt_nn_to_half_rows(_p(src), int(rows), int(cols), float(scale), _p(dst),
+                                            int(dst.shape[-1]), _s()))
 
 
 def smrt_nn_bias_act(x, bias, act, z, a):

@@ -46,6 +46,10 @@ def re_feature(re: float) -> float:
     return (math.log(re) - math.log(RE_LO)) / (math.log(RE_HI) - math.log(RE_LO))
 
 
+def _pad8(n: int) -> int:
+    return (n + 7) // 8 * 8
+
+
 class UNet:
     def __init__(self, base: int = 32, cin: int = 3, cout: int = 3, seed: int = 0, device: str = "cuda",
                  gemm: str = "tcgen05"):
@@ -118,44 +122,62 @@ class UNet:
         n, h, w, _ = x.shape
         rows = n * h * w
         kk = k * k * ci
-        col = t.empty((rows, kk), dtype=t.float16, device=self.device)
-        if k == 3:
-            K.smrt_nn_im2col3(x, col)
-        else:
-            K.smrt_nn_to_half(x, col)
         y = t.empty((n, h, w, co), dtype=t.float32, device=self.device)
-        self._gemm(0, 1, rows, co, kk, 1.0, col, kk, self._wh[name], kk, 0.0, y, co)
+        if self._implicit(k, ci):
+            # implicit GEMM: the A tiles are gathered from x, no im2col matrix is built
+            K.smrt_nn_conv3_tc(x, self._wh[name], y, 1.0, 0.0, self._gemm_err)
+            col = None
+        else:
+            ldk = _pad8(kk)             # whole 16-byte rows for the GEMM's vector loads
+            col = t.empty((rows, ldk), dtype=t.float16, device=self.device)
+            if k == 3:
+                K.smrt_nn_im2col3(x, col)
+            else:
+                K.smrt_nn_to_half_rows(x.view(rows, ci), col)
+            self._gemm(0, 1, rows, co, kk, 1.0, col, ldk, self._wh[name], kk, 0.0, y, co)
         z = t.empty_like(y) if (act and cache is not None) else None
         K.smrt_nn_bias_act(y, self.params[name + ".b"], act, z, y)
         if cache is not None:
-            cache[name] = (col, z, x.shape)
+            cache[name] = (col, z, x)
         return y
+
+    def _implicit(self, k, c):
+        """3x3 convolutions over C % 8 == 0 channels run as implicit GEMMs on the tcgen05 backend."""
+        return self.gemm_backend == "tcgen05" and k == 3 and c % 8 == 0
 
     def _conv_bwd(self, spec, da, cache, need_dx=True):
         t = self.torch
         name, ci, co, k, act = spec
-        col, z, xshape = cache[name]
+        col, z, x = cache[name]
+        xshape = x.shape
         n, h, w, _ = xshape
         rows = n * h * w
         kk = k * k * ci
+        if col is None:             # the forward gathered from x; the weight gradient needs the matrix
+            col = t.empty((rows, _pad8(kk)), dtype=t.float16, device=self.device)
+            K.smrt_nn_im2col3(x, col)
+        ldk, ldz = col.shape[1], _pad8(co)
         dz = t.empty_like(da)
         K.smrt_nn_bias_act_bwd(da, z, act, dz, self.grads[name + ".b"])
-        dzh = t.empty(dz.shape, dtype=t.float16, device=self.device)
-        K.smrt_nn_to_half(dz, dzh)
+        dzh = t.empty((rows, ldz), dtype=t.float16, device=self.device)
+        K.smrt_nn_to_half_rows(dz.view(rows, co), dzh)
         split = max(1, min(256, rows // 8192))
         gw = self.grads[name + ".w"]
         if self.gemm_backend == "tcgen05":
             # dW^T = col^T dz: the 9 cin dimension on the tensor core's M = 128 side, stored transposed
-            K.smrt_nn_gemm_tc(1, 2, kk, co, rows, 1.0, col, kk, dzh, co, 1.0, gw, kk, split, self._gemm_err)
+            K.smrt_nn_gemm_tc(1, 2, kk, co, rows, 1.0, col, ldk, dzh, ldz, 1.0, gw, kk, split, self._gemm_err)
         else:
-            self._gemm(1, 0, co, kk, rows, 1.0, dzh, co, col, kk, 1.0, gw, kk, split)
+            self._gemm(1, 0, co, kk, rows, 1.0, dzh, ldz, col, ldk, 1.0, gw, kk, split)
         if not need_dx:
             return None
         dx = t.empty(xshape, dtype=t.float32, device=self.device)
         if k == 1:
-            self._gemm(0, 0, rows, ci, co, 1.0, dzh, co, self._wh[name], ci, 0.0, dx, ci)
+            self._gemm(0, 0, rows, ci, co, 1.0, dzh, ldz, self._wh[name], ci, 0.0, dx, ci)
             return dx
         # dx = im2col(dz) * flip(W)^T: the adjoint 3x3 convolution, no col2im
+        if self._implicit(k, co):
+            K.smrt_nn_conv3_tc(dz.view(n, h, w, co), self._wf[name], dx, 1.0, 0.0, self._gemm_err)
+            return dx
         dzcol = t.empty((rows, 9 * co), dtype=t.float16, device=self.device)
         K.smrt_nn_im2col3(dz.view(n, h, w, co), dzcol)
         self._gemm(0, 1, rows, ci, 9 * co, 1.0, dzcol, 9 * co, self._wf[name], 9 * co, 0.0, dx, ci)

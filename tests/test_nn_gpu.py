@@ -61,6 +61,31 @@ def test_im2col_col2im_match_oracle():
     assert np.abs(_np(dx) - U.col2im3(d, (2, 6, 10, 5))).max() < 1e-5
 
 
+@pytest.mark.parametrize("C,ld", [(5, 48), (8, 72), (16, 144), (3, 32)])
+def test_im2col_vector_and_padded_rows(C, ld):
+    """The 16-byte path (C % 8 == 0, dense rows) and padded rows (zeroed pad columns), ragged H, W."""
+    import torch
+    r = _rng(30 + C)
+    x = r.normal(size=(3, 7, 11, C))
+    col = torch.full((3 * 7 * 11, ld), float("nan"), dtype=torch.float16, device="cuda")
+    S.smrt_nn_im2col3(_t(x), col)
+    got = _np(col)
+    ref = U.im2col3(x.astype(np.float32).astype(np.float16).astype(np.float64))
+    assert np.array_equal(got[:, :9 * C], ref)
+    assert (got[:, 9 * C:] == 0).all()
+
+
+def test_to_half_rows_pads_with_zeros():
+    import torch
+    r = _rng(40)
+    a = r.normal(size=(37, 3))
+    d = torch.full((37, 8), float("nan"), dtype=torch.float16, device="cuda")
+    S.smrt_nn_to_half_rows(_t(a), d, 2.0)
+    got = _np(d)
+    assert np.array_equal(got[:, :3], (2.0 * a).astype(np.float32).astype(np.float16).astype(np.float64))
+    assert (got[:, 3:] == 0).all()
+
+
 def test_bias_act_forward_backward():
     import torch
     r = _rng(4)
@@ -155,10 +180,12 @@ def test_resize_bilinear_special_cases():
 
 
 @pytest.mark.parametrize("backend", ["tcgen05", "wmma"])
-def test_unet_loss_and_gradients_match_oracle(backend):
-    """Same weights, same batch: loss and every gradient tensor within half-precision operand rounding."""
+@pytest.mark.parametrize("n,h", [(2, 16), (1, 128)], ids=["2x16", "1x128"])
+def test_unet_loss_and_gradients_match_oracle(backend, n, h):
+    """Same weights, same batch: loss and every gradient tensor within half-precision operand rounding.
+    At 128^2 the weight gradients of the top level run split-K (atomic partial sums)."""
     from paper_2409_01076_gb300.unet import UNet
-    base, n, h, w = 8, 2, 16, 16
+    base, w = 8, h
     params = U.init_params(base, seed=3)
     r = _rng(8)
     x = r.uniform(0, 1, size=(n, h, w, 3))
