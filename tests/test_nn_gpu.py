@@ -206,6 +206,32 @@ def test_unet_loss_and_gradients_match_oracle(backend, n, h):
         assert net.gemm_timeouts() == 0
 
 
+@pytest.mark.parametrize("backend", ["tcgen05", "wmma"])
+def test_unet_gradients_match_oracle_at_training_size(backend):
+    """The warm-start network itself (32 base channels) on a 256^2 input: implicit-GEMM and split-K
+    paths at full size.  Every gradient within 5e-3 of the FP64 oracle (half-operand rounding gives
+    ~1e-3), cosine > 0.99999."""
+    from paper_2409_01076_gb300.unet import UNet
+    base, n, h, w = 32, 1, 256, 256
+    params = U.init_params(base, seed=3)
+    r = _rng(12)
+    x = r.uniform(0, 1, size=(n, h, w, 3))
+    t = 0.3 * r.normal(size=(n, h, w, 3))
+    loss_ref, grads_ref, _ = U.loss_and_grads(params, x, t, base)
+    net = UNet(base=base, gemm=backend)
+    net.load_numpy(params)
+    net.grad_scale = 1024.0
+    net.loss_and_grad(_t(x), _t(t))
+    assert abs(float(_np(net._loss)[0]) / loss_ref - 1) < 1e-4
+    for key, gr in grads_ref.items():
+        g = _np(net.grads[key]) / net.grad_scale
+        rel = np.linalg.norm(g - gr) / max(np.linalg.norm(gr), 1e-30)
+        cos = (g * gr).sum() / max(np.linalg.norm(g) * np.linalg.norm(gr), 1e-30)
+        assert rel < 5e-3 and cos > 0.99999, (key, rel, cos)
+    if backend == "tcgen05":
+        assert net.gemm_timeouts() == 0
+
+
 def test_unet_training_reduces_the_loss():
     from paper_2409_01076_gb300.unet import UNet, input_grid
     net = UNet(base=8, seed=1)
