@@ -62,7 +62,8 @@ def parse_args(argv=None):
                    help="batched-throughput: this tile shape (smrt_batch_set_shape) instead of autotuning")
     p.add_argument("--unet-batch", type=int, default=16)
     p.add_argument("--unet-iters", type=int, default=10)
-    p.add_argument("--unet-backend", choices=["both", "tcgen05", "wmma"], default="both")
+    p.add_argument("--unet-backend", choices=["all", "tcgen05", "tcgen05-gather", "wmma"], default="all",
+                   help="tcgen05: TMA-fed convolutions; tcgen05-gather: thread-gathered A tiles; wmma: legacy MMA")
     p.add_argument("--tol", type=float, default=1e-7)
     p.add_argument("--residual", choices=["stride", "step"], default="stride",
                    help="batched report: stride (mean change per update over a check) or one-step residual")
@@ -707,8 +708,10 @@ def unet_report(args):
     g = torch.Generator(device="cuda").manual_seed(0)
     target = 0.1 * torch.randn((B, 256, 256, 3), device="cuda", generator=g)
     out = {"report": "unet", "batch": B, "side": 256, "base_channels": 32, "iters": args.unet_iters}
-    for backend in (("tcgen05", "wmma") if args.unet_backend == "both" else (args.unet_backend,)):
-        net = UNet(base=32, gemm=backend)
+    variants = {"tcgen05": ("tcgen05", "tma"), "tcgen05-gather": ("tcgen05", "gather"), "wmma": ("wmma", "gather")}
+    for backend in (list(variants) if args.unet_backend == "all" else [args.unet_backend]):
+        gemm, conv = variants[backend]
+        net = UNet(base=32, gemm=gemm, conv=conv)
         for _ in range(3):
             net.train_step(x, target, 1e-3)
         torch.cuda.synchronize()

@@ -58,6 +58,29 @@ SMRT_API int smrt_nn_gemm_tc(int transA, int transB, int M, int N, int K, float 
 SMRT_API int smrt_nn_conv3_tc(const float *x, int N, int H, int W, int C, const void *w, int cout, float alpha,
                               float beta, float *y, int ldy, int *err, void *stream);
 
+/* The same 3x3 convolution as smrt_nn_conv3_tc with both operands delivered by TMA
+ * (cp.async.bulk.tensor) into shared memory, and the nine filter taps taken as shifted views of
+ * one zero-padded input tile instead of an im2col tile:
+ *   y[p][o] = alpha * sum_{tap, c} xh[n][yy+ky-1][xx+kx-1][c] * w[o][tap*C + c] + beta * y[p][o].
+ * xh: N x H x W x C HALF activations (NHWC, dense, 16-byte aligned), C % 16 == 0; values outside
+ * the image are zero.  wp: the weights w (cout x 9C half, the layout of smrt_nn_conv3_tc) packed by
+ * smrt_nn_pack3 (16-byte aligned).  y: N*H*W rows of ldy >= cout float32.  Each 128-thread block
+ * computes 16 rows x 8 pixels of one image by 32, 64 or 128 output channels; K runs over 16-channel
+ * chunks through up to four mbarrier-tracked stages (a TMA producer lane and a tcgen05.mma issuer
+ * lane), accumulator in tensor memory, tcgen05.ld epilogue.  Accumulation order is chunk-major
+ * (all nine taps of channels 0-15, then of 16-31, ...), so results equal smrt_nn_conv3_tc's up to
+ * float32 rounding, not bit for bit.  err as in smrt_nn_gemm_tc (every wait is bounded, here by
+ * one second of the GPU's global timer).  SMRT_ERR_ARG for C % 16 != 0, misaligned xh / wp or
+ * sizes the grid cannot cover; SMRT_ERR_CUDA if the driver rejects a tensor map. */
+SMRT_API int smrt_nn_conv3_tma(const void *xh, int N, int H, int W, int C, const void *wp, int cout, float alpha,
+                               float beta, float *y, int ldy, int *err, void *stream);
+
+/* Packs 3x3 weights w (cout x 9C half, column tap*C + c) for smrt_nn_conv3_tma:
+ *   wp[((chunk*9 + tap)*2 + q)*cout*8 + o*8 + e] = w[o][tap*C + chunk*16 + q*8 + e]
+ * (chunk = c / 16, q = (c % 16) / 8, e = c % 8), so that all nine taps of one 16-channel chunk
+ * are one contiguous K-major block.  wp holds 9*C*cout halves.  C % 16 == 0. */
+SMRT_API int smrt_nn_pack3(const void *w, int cout, int C, void *wp, void *stream);
+
 /* 3x3, stride 1, zero padding 1 patches of x (N,H,W,C float32) into col (N*H*W rows of
  * ld >= 9*C halves, row-major): col[p*ld + (ky*3+kx)*C + c] = x[n][y+ky-1][x+kx-1][c].
  * Columns 9*C .. ld-1 are set to zero (a padded ld lets a GEMM read whole 16-byte rows). */

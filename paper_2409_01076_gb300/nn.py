@@ -44,6 +44,18 @@ def smrt_nn_conv3_tc(x, w, y, alpha=1.0, beta=0.0, err=None):
                                         int(y.shape[-1]), _p(err), _s()))
 
 
+def smrt_nn_conv3_tma(xh, wp, y, cout, alpha=1.0, beta=0.0, err=None):
+    """xh: (N, H, W, C) half; wp: 9*C*cout halves from smrt_nn_pack3; y: N*H*W rows of cout float32."""
+    n, h, wd, c = xh.shape
+    _check(_lib.load().smrt_nn_conv3_tma(_p(xh), n, h, wd, c, _p(wp), int(cout), float(alpha), float(beta), _p(y),
+                                         int(y.shape[-1]), _p(err), _s()))
+
+
+def smrt_nn_pack3(w, C, wp):
+    """w: (cout, 9C) half; wp: 9*C*cout halves (any shape)."""
+    _check(_lib.load().smrt_nn_pack3(_p(w), int(w.shape[0]), int(C), _p(wp), _s()))
+
+
 def smrt_nn_im2col3(x, col):
     """col: (N*H*W, ld) half with ld >= 9*C (the row stride is taken from col)."""
     n, h, w, c = x.shape

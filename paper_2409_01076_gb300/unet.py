@@ -52,7 +52,7 @@ def _pad8(n: int) -> int:
 
 class UNet:
     def __init__(self, base: int = 32, cin: int = 3, cout: int = 3, seed: int = 0, device: str = "cuda",
-                 gemm: str = "tcgen05"):
+                 gemm: str = "tcgen05", conv: str = "tma"):
         import torch
         self.torch = torch
         self.base, self.cin, self.cout, self.device = base, cin, cout, device
@@ -79,6 +79,9 @@ class UNet:
         if gemm not in ("tcgen05", "wmma"):
             raise ValueError("gemm must be 'tcgen05' or 'wmma'")
         self.gemm_backend = gemm
+        if conv not in ("tma", "gather"):
+            raise ValueError("conv must be 'tma' or 'gather'")
+        self.conv_path = conv           # tcgen05 3x3 convolutions: TMA halo tiles, or thread-gathered A tiles
         self._gemm_err = torch.zeros(1, dtype=torch.int32, device=device)   # tensor-core wait timeouts
 
     def _gemm(self, transA, transB, M, N, Kd, alpha, A, lda, B, ldb, beta, C, ldc, split=1):
@@ -105,16 +108,22 @@ class UNet:
     # ---- one convolution (3x3 via im2col, or 1x1) ----------------------------------------
     def _half_weights(self):
         t = self.torch
-        self._wh, self._wf = {}, {}
+        self._wh, self._wf, self._wp, self._wfp = {}, {}, {}, {}
         for name, ci, co, k, _ in self.specs:
             w = self.params[name + ".w"]
             h = t.empty(w.shape, dtype=t.float16, device=self.device)
             K.smrt_nn_to_half(w, h)
             self._wh[name] = h
+            if self._tma(k, ci):                # packed for the TMA convolution
+                self._wp[name] = t.empty(9 * ci * co, dtype=t.float16, device=self.device)
+                K.smrt_nn_pack3(h, ci, self._wp[name])
             if k == 3 and name != "enc1a":      # weights of the adjoint convolution (input gradient)
                 f = t.empty((ci, 9 * co), dtype=t.float16, device=self.device)
                 K.smrt_nn_flip3(w, f)
                 self._wf[name] = f
+                if self._tma(k, co):
+                    self._wfp[name] = t.empty(9 * ci * co, dtype=t.float16, device=self.device)
+                    K.smrt_nn_pack3(f, co, self._wfp[name])
 
     def _conv(self, spec, x, cache):
         t = self.torch
@@ -123,7 +132,13 @@ class UNet:
         rows = n * h * w
         kk = k * k * ci
         y = t.empty((n, h, w, co), dtype=t.float32, device=self.device)
-        if self._implicit(k, ci):
+        if self._tma(k, ci):
+            # operands by TMA: half activations, nine taps as shifted views of one haloed tile
+            xh = t.empty((n, h, w, ci), dtype=t.float16, device=self.device)
+            K.smrt_nn_to_half(x, xh)
+            K.smrt_nn_conv3_tma(xh, self._wp[name], y, co, 1.0, 0.0, self._gemm_err)
+            col = None
+        elif self._implicit(k, ci):
             # implicit GEMM: the A tiles are gathered from x, no im2col matrix is built
             K.smrt_nn_conv3_tc(x, self._wh[name], y, 1.0, 0.0, self._gemm_err)
             col = None
@@ -144,6 +159,10 @@ class UNet:
     def _implicit(self, k, c):
         """3x3 convolutions over C % 8 == 0 channels run as implicit GEMMs on the tcgen05 backend."""
         return self.gemm_backend == "tcgen05" and k == 3 and c % 8 == 0
+
+    def _tma(self, k, c):
+        """... and with TMA-fed operands when C % 16 == 0, unless the gather path was chosen."""
+        return self.conv_path == "tma" and self._implicit(k, c) and c % 16 == 0
 
     def _conv_bwd(self, spec, da, cache, need_dx=True):
         t = self.torch
@@ -175,6 +194,9 @@ class UNet:
             self._gemm(0, 0, rows, ci, co, 1.0, dzh, ldz, self._wh[name], ci, 0.0, dx, ci)
             return dx
         # dx = im2col(dz) * flip(W)^T: the adjoint 3x3 convolution, no col2im
+        if self._tma(k, co):
+            K.smrt_nn_conv3_tma(dzh.view(n, h, w, co), self._wfp[name], dx, ci, 1.0, 0.0, self._gemm_err)
+            return dx
         if self._implicit(k, co):
             K.smrt_nn_conv3_tc(dz.view(n, h, w, co), self._wf[name], dx, 1.0, 0.0, self._gemm_err)
             return dx

@@ -179,9 +179,13 @@ def test_resize_bilinear_special_cases():
     assert np.abs(_np(out)[:, inner, inner] - ref[:, inner, inner]).max() < 1e-5
 
 
-@pytest.mark.parametrize("backend", ["tcgen05", "wmma"])
+BACKENDS = [("tcgen05", "tma"), ("tcgen05", "gather"), ("wmma", "gather")]
+BACKEND_IDS = ["tcgen05-tma", "tcgen05-gather", "wmma"]
+
+
+@pytest.mark.parametrize("backend,conv", BACKENDS, ids=BACKEND_IDS)
 @pytest.mark.parametrize("n,h", [(2, 16), (1, 128)], ids=["2x16", "1x128"])
-def test_unet_loss_and_gradients_match_oracle(backend, n, h):
+def test_unet_loss_and_gradients_match_oracle(backend, conv, n, h):
     """Same weights, same batch: loss and every gradient tensor within half-precision operand rounding.
     At 128^2 the weight gradients of the top level run split-K (atomic partial sums)."""
     from paper_2409_01076_gb300.unet import UNet
@@ -191,7 +195,7 @@ def test_unet_loss_and_gradients_match_oracle(backend, n, h):
     x = r.uniform(0, 1, size=(n, h, w, 3))
     t = 0.3 * r.normal(size=(n, h, w, 3))
     loss_ref, grads_ref, _ = U.loss_and_grads(params, x, t, base)
-    net = UNet(base=base, gemm=backend)
+    net = UNet(base=base, gemm=backend, conv=conv)
     net.load_numpy(params)
     net.grad_scale = 1024.0
     net.loss_and_grad(_t(x), _t(t))
@@ -206,8 +210,8 @@ def test_unet_loss_and_gradients_match_oracle(backend, n, h):
         assert net.gemm_timeouts() == 0
 
 
-@pytest.mark.parametrize("backend", ["tcgen05", "wmma"])
-def test_unet_gradients_match_oracle_at_training_size(backend):
+@pytest.mark.parametrize("backend,conv", BACKENDS, ids=BACKEND_IDS)
+def test_unet_gradients_match_oracle_at_training_size(backend, conv):
     """The warm-start network itself (32 base channels) on a 256^2 input: implicit-GEMM and split-K
     paths at full size.  Every gradient within 5e-3 of the FP64 oracle (half-operand rounding gives
     ~1e-3), cosine > 0.99999."""
@@ -218,7 +222,7 @@ def test_unet_gradients_match_oracle_at_training_size(backend):
     x = r.uniform(0, 1, size=(n, h, w, 3))
     t = 0.3 * r.normal(size=(n, h, w, 3))
     loss_ref, grads_ref, _ = U.loss_and_grads(params, x, t, base)
-    net = UNet(base=base, gemm=backend)
+    net = UNet(base=base, gemm=backend, conv=conv)
     net.load_numpy(params)
     net.grad_scale = 1024.0
     net.loss_and_grad(_t(x), _t(t))
