@@ -58,28 +58,54 @@ SMRT_API int smrt_nn_gemm_tc(int transA, int transB, int M, int N, int K, float 
 SMRT_API int smrt_nn_conv3_tc(const float *x, int N, int H, int W, int C, const void *w, int cout, float alpha,
                               float beta, float *y, int ldy, int *err, void *stream);
 
-/* The same 3x3 convolution as smrt_nn_conv3_tc with both operands delivered by TMA
- * (cp.async.bulk.tensor) into shared memory, and the nine filter taps taken as shifted views of
- * one zero-padded input tile instead of an im2col tile:
- *   y[p][o] = alpha * sum_{tap, c} xh[n][yy+ky-1][xx+kx-1][c] * w[o][tap*C + c] + beta * y[p][o].
- * xh: N x H x W x C HALF activations (NHWC, dense, 16-byte aligned), C % 16 == 0; values outside
- * the image are zero.  wp: the weights w (cout x 9C half, the layout of smrt_nn_conv3_tc) packed by
- * smrt_nn_pack3 (16-byte aligned).  y: N*H*W rows of ldy >= cout float32.  Each 128-thread block
- * computes 16 rows x 8 pixels of one image by 32, 64 or 128 output channels; K runs over 16-channel
- * chunks through up to four mbarrier-tracked stages (a TMA producer lane and a tcgen05.mma issuer
- * lane), accumulator in tensor memory, tcgen05.ld epilogue.  Accumulation order is chunk-major
- * (all nine taps of channels 0-15, then of 16-31, ...), so results equal smrt_nn_conv3_tc's up to
- * float32 rounding, not bit for bit.  err as in smrt_nn_gemm_tc (every wait is bounded, here by
- * one second of the GPU's global timer).  SMRT_ERR_ARG for C % 16 != 0, misaligned xh / wp or
- * sizes the grid cannot cover; SMRT_ERR_CUDA if the driver rejects a tensor map. */
-SMRT_API int smrt_nn_conv3_tma(const void *xh, int N, int H, int W, int C, const void *wp, int cout, float alpha,
+/* ---- TMA-fed 3x3 convolutions ---------------------------------------------------------------
+ * These read HALF activations in the channel-group-blocked layout xb[n][c/8][y][x][c%8]
+ * ([N][C/8][H][W][8], dense, 16-byte aligned), which smrt_nn_to_half_blocked writes: one image row of
+ * one 8-channel group is then W*16 contiguous bytes, so one TMA box brings a whole zero-padded
+ * 18 x 10 pixel window as 18 runs of 160 bytes.  Each 128-thread block works on a 16-row x 8-pixel
+ * output tile; the nine taps of the filter are nine shifted shared-memory views of that one window
+ * (no im2col tile).  A TMA producer lane and a tcgen05.mma issuer lane run an mbarrier pipeline;
+ * the float32 accumulator lives in tensor memory.  err as in smrt_nn_gemm_tc: every wait is
+ * bounded (here by one second of the GPU's global timer).  SMRT_ERR_ARG for unsupported channel
+ * counts, misaligned pointers or sizes the grid cannot cover; SMRT_ERR_CUDA if the driver rejects a
+ * tensor map. */
+
+/* xb = half(scale * x) in the blocked layout above; x is NHWC float32 (16-byte aligned), C % 8 == 0. */
+SMRT_API int smrt_nn_to_half_blocked(const float *x, int N, int H, int W, int C, float scale, void *xb,
+                                     void *stream);
+
+/* Halves that smrt_nn_pack3 writes for (cout, C): 9 * C * cout rounded up to whole output-channel
+ * tiles (32 if cout <= 32, 64 if cout <= 64, else multiples of 128); -1 if C % 16 != 0 or cout < 1. */
+SMRT_API long long smrt_nn_pack3_halves(int cout, int C);
+
+/* Packs 3x3 weights w (cout x 9C half, column tap*C + c, the layout of smrt_nn_conv3_tc) for
+ * smrt_nn_conv3_tma, with TN the output-channel tile above and nb = o / TN, r = o % TN:
+ *   wp[(((nb*(C/16) + c/16)*18 + tap*2 + (c%16)/8)*TN + r)*8 + c%8] = w[o][tap*C + c]
+ * (zero for o >= cout), so that the operand of one pipeline stage -- all nine taps of 16 input
+ * channels for one output-channel tile -- is one contiguous block, copied by one bulk copy.
+ * wp: smrt_nn_pack3_halves(cout, C) halves, 16-byte aligned.  C % 16 == 0. */
+SMRT_API int smrt_nn_pack3(const void *w, int cout, int C, void *wp, void *stream);
+
+/* 3x3, stride 1, zero padding 1 convolution:
+ *   y[p][o] = alpha * sum_{tap, c} x[n][yy+ky-1][xx+kx-1][c] * w[o][tap*C + c] + beta * y[p][o]
+ * for p = (n*H + yy)*W + xx, with x given blocked as xb (C % 16 == 0) and w packed as wp.  y: N*H*W
+ * rows of ldy >= cout float32.  Output-channel tiles of 32, 64 or 128; K runs over 16-channel chunks
+ * (one TMA of two halo planes and one bulk copy of weights per stage, up to four stages).  The sum
+ * runs chunk-major (all nine taps of channels 0-15, then of 16-31, ...), so results equal
+ * smrt_nn_conv3_tc's up to float32 rounding, not bit for bit.  The input gradient of a convolution
+ * is this call on dz with the weights of smrt_nn_flip3. */
+SMRT_API int smrt_nn_conv3_tma(const void *xb, int N, int H, int W, int C, const void *wp, int cout, float alpha,
                                float beta, float *y, int ldy, int *err, void *stream);
 
-/* Packs 3x3 weights w (cout x 9C half, column tap*C + c) for smrt_nn_conv3_tma:
- *   wp[((chunk*9 + tap)*2 + q)*cout*8 + o*8 + e] = w[o][tap*C + chunk*16 + q*8 + e]
- * (chunk = c / 16, q = (c % 16) / 8, e = c % 8), so that all nine taps of one 16-channel chunk
- * are one contiguous K-major block.  wp holds 9*C*cout halves.  C % 16 == 0. */
-SMRT_API int smrt_nn_pack3(const void *w, int cout, int C, void *wp, void *stream);
+/* Weight gradient of the same convolution, ACCUMULATED into gw (cout rows of ldg >= 9C float32):
+ *   gw[o][tap*C + c] += alpha * sum_p x[n][yy+ky-1][xx+kx-1][c] * dz[p][o]
+ * with x and dz both blocked half (xb: C channels, dzb: cout channels, C % 8 == 0, cout % 8 == 0).
+ * Blocks of 128 input x 32 output channels; each block sums a run of pixel tiles for all nine taps
+ * in tensor memory (both operands MN-major views of the TMA tiles: K is the pixel index) and adds
+ * its result with float32 atomics, so the summation order -- and the last bits -- vary from run to
+ * run. */
+SMRT_API int smrt_nn_conv3_wgrad_tma(const void *xb, int N, int H, int W, int C, const void *dzb, int cout,
+                                     float alpha, float *gw, int ldg, int *err, void *stream);
 
 /* 3x3, stride 1, zero padding 1 patches of x (N,H,W,C float32) into col (N*H*W rows of
  * ld >= 9*C halves, row-major): col[p*ld + (ky*3+kx)*C + c] = x[n][y+ky-1][x+kx-1][c].

@@ -58,9 +58,13 @@ SIGNATURES = [
                                 ctypes.c_float, c_void_p, c_int, c_int, c_void_p, c_void_p]),
     ("smrt_nn_conv3_tc", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_int, ctypes.c_float,
                                  ctypes.c_float, c_void_p, c_int, c_void_p, c_void_p]),
+    ("smrt_nn_to_half_blocked", c_int, [c_void_p, c_int, c_int, c_int, c_int, ctypes.c_float, c_void_p, c_void_p]),
+    ("smrt_nn_pack3_halves", c_longlong, [c_int, c_int]),
+    ("smrt_nn_pack3", c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p]),
     ("smrt_nn_conv3_tma", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_int, ctypes.c_float,
                                   ctypes.c_float, c_void_p, c_int, c_void_p, c_void_p]),
-    ("smrt_nn_pack3", c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p]),
+    ("smrt_nn_conv3_wgrad_tma", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_int, ctypes.c_float,
+                                        c_void_p, c_int, c_void_p, c_void_p]),
     ("smrt_nn_im2col3", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_int, c_void_p]),
     ("smrt_nn_col2im3", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p]),
     ("smrt_nn_flip3", c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p]),

@@ -1,36 +1,35 @@
-// nn_tma.cu -- smrt_nn_conv3_tma and smrt_nn_pack3: a 3x3 convolution on the 5th-generation
-// tensor cores whose operands arrive by TMA (cp.async.bulk.tensor), with the nine taps of the
-// filter read as nine shifted views of ONE haloed input tile -- no im2col tile is ever written.
+// nn_tma.cu -- 3x3 convolutions on the 5th-generation tensor cores with operands delivered by TMA
+// (cp.async.bulk.tensor / cp.async.bulk), where the nine taps of the filter are nine shifted views
+// of ONE haloed input tile in shared memory: no im2col matrix or tile is ever written.
 //
-// Output tile of a CTA: 16 image rows x 8 pixels of one image (the GEMM's M = 128 rows; row m is
-// pixel (y0 + m / 8, x0 + m % 8)) by TN output channels (TN = 32, 64 or 128).
+//   smrt_nn_to_half_blocked  float32 NHWC -> half, channel-group-blocked [N][C/8][H][W][8]
+//   smrt_nn_pack3            3x3 weights -> [n-block][16-channel chunk][9 taps x 2 groups][TN][8]
+//   smrt_nn_conv3_tma        y = conv3x3(x, w)            (forward; input gradient with flipped w)
+//   smrt_nn_conv3_wgrad_tma  dW += sum_pixels x(shifted) dz  (weight gradient)
 //
-// Input tile: the 18 x 10 window around it (one pixel of halo on every side).  Per group of 8
-// input channels it is one "plane" [18 rows][10 pixels][8 halves] = 2,880 B in shared memory,
-// written by one 4-D TMA load of the NHWC half activations with the box {8, 10, 18, 1} at
-// (c, x0 - 1, y0 - 1, n); TMA fills the part outside the image with zeros, which is exactly the
-// convolution's zero padding.  Planes are 2,944 B apart (a multiple of 128 B, as TMA wants).
+// Blocked activations.  In [N][C/8][H][W][8] one image row of one 8-channel group is W * 16
+// contiguous bytes, so a TMA box over the 4-D view (8W halves, H, C/8, N) brings 18 halo rows of
+// 10 pixels x 8 channels as 18 runs of 160 B (an NHWC box would need 180 runs of 16 B).  A box
+// starting at x = 8 (x0 - 1) is 16-byte aligned, and TMA fills everything outside the image with
+// zeros -- exactly the convolution's zero padding.
 //
-// Why no im2col: 8 consecutive pixels of one plane row are 128 contiguous bytes -- one core
-// matrix of the no-swizzle K-major operand layout (8 GEMM rows x 8 K halves).  So for tap
-// (ky, kx) the GEMM's A operand (rows = the 128 output pixels, K = 16 input channels) is the
-// shared-memory descriptor
-//     start = plane(q) + (ky * 10 + kx) * 16 B,
-//     leading byte offset (next 8 channels, K direction)    = plane stride  = 2,944 B,
-//     stride byte offset  (next 8 pixels = next image row)  = 10 * 16 B     =   160 B.
-// The weights come pre-packed by smrt_nn_pack3 so that one 3-D TMA load brings all nine taps of a
-// 16-channel chunk in the matching K-major layout [9 taps x 2 groups][TN][8 halves].
+// Tiles.  An output tile is 16 image rows x 8 pixels (the GEMM's 128 rows; row m is pixel
+// (y0 + m / 8, x0 + m % 8)).  Its input window is 18 x 10 pixels, stored per 8-channel group as a
+// "plane" [18 rows][10 px][8 halves] of 2,880 B.  Eight consecutive pixels of a plane row are 128
+// contiguous bytes: one core matrix of the no-swizzle operand layouts.  Hence, for tap (ky, kx):
+//   forward (K = channels, K-major A): start = plane(q) + (ky*10 + kx)*16 B, leading byte offset
+//     (next 8 channels) = 2,880 B, stride byte offset (next 8 pixels = next image row) = 160 B;
+//   weight gradient (K = pixels, MN-major A with M = channels): start = plane(0) +
+//     ((2j + ky)*10 + kx)*16 B for pixel rows 2j, 2j+1, leading byte offset (next 8 pixels = next
+//     image row) = 160 B, stride byte offset (next 8 channels) = 2,880 B.
 //
-// Pipeline (128 threads, roles in warp 0 and warp 1; the K loop runs over 16-channel chunks):
-//   producer (warp 0, one lane): per chunk, wait until the stage is free, arm its "full"
-//     mbarrier with the byte count and issue 3 TMA loads (two planes, one weight slab);
-//   MMA issuer (warp 1, one lane): per chunk, wait for "full", issue nine tcgen05.mma
-//     (M 128, N TN, K 16, half x half -> f32, accumulator in tensor memory), commit to the stage's
-//     "empty" mbarrier; after the last chunk commit to "done";
-//   epilogue (all 4 warps): wait for "done", tcgen05.ld the accumulator rows, y = alpha acc + beta y.
-// Every mbarrier wait is bounded by 1 s of %globaltimer.  A wait that gives up sets *err and the
-// CTA's failed flag, waits once more with the same bound (so no copy or MMA is left in flight
-// where avoidable), skips the epilogue, and the CTA still releases its tensor memory.
+// Pipelines.  128 threads; lane 0 of warp 0 is the TMA producer, lane 0 of warp 1 issues the
+// tcgen05.mma (half x half -> float32, accumulator in tensor memory), all four warps run the
+// tcgen05.ld epilogue.  Stages are tracked by "full" (TMA transaction bytes) and "empty"
+// (tcgen05.commit) mbarriers; a final commit to "done" releases the epilogue.  Every wait is
+// bounded by 1 s of %globaltimer: a wait that gives up sets *err and the CTA's failed flag, waits
+// once more with the same bound (so no copy or MMA is left in flight where avoidable), skips the
+// epilogue, and the CTA still releases its tensor memory.
 #include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -46,22 +45,26 @@ namespace {
 
 constexpr int kTileRows = 16, kTilePx = 8;                 // output tile: 16 rows x 8 pixels
 constexpr int kHaloRows = kTileRows + 2, kHaloPx = kTilePx + 2;
-constexpr int kChunk = 16;                                 // input channels per pipeline stage
-constexpr int kPlaneBytes = kHaloRows * kHaloPx * 16;      // 2,880 B written by one TMA
-constexpr int kPlaneStride = 2944;                         // 23 x 128 B
-constexpr int kASlab = 2 * kPlaneStride;                   // two planes per 16-channel chunk
-constexpr int kMaxStages = 4;
+constexpr int kChunk = 16;                                 // input channels per forward stage
+constexpr int kPlane = kHaloRows * kHaloPx * 16;           // 2,880 B: one halo plane
+constexpr int kDzPlane = kTileRows * kTilePx * 16;         // 2,048 B: one 8-channel plane of dz
+constexpr int kFwdStages = 4;
+constexpr int kWgStages = 6;
+constexpr int kWgTN = 32;                                  // output channels per weight-gradient CTA
+constexpr int kWgPlanes = 16;                              // input channels per weight-gradient CTA / 8
 constexpr unsigned long long kWaitNs = 1000000000ull;      // a wait gives up after 1 s (%globaltimer)
 
-static_assert(kPlaneStride >= kPlaneBytes && kPlaneStride % 128 == 0, "plane stride");
 static_assert(kTileRows * kTilePx == 128, "M = 128");
 
+int tile_n(int cout) { return cout <= 32 ? 32 : cout <= 64 ? 64 : 128; }
+
 template <int TN>
-constexpr int stage_bytes()
+constexpr int fwd_stage_bytes()
 {
-    // A: two planes; B: 18 slabs of TN rows x 16 B; rounded up to 1 KB
-    return ((kASlab + 18 * TN * 16) + 1023) / 1024 * 1024;
+    // A: two planes (rounded up to 128 B); B: 18 slabs of TN rows x 16 B; rounded up to 1 KB
+    return ((2 * kPlane + 127) / 128 * 128 + 18 * TN * 16 + 1023) / 1024 * 1024;
 }
+constexpr int kFwdA = (2 * kPlane + 127) / 128 * 128;      // 5,760 B
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -79,11 +82,13 @@ __device__ __forceinline__ unsigned long long desc(uint32_t saddr, uint32_t lbo,
     return d;
 }
 
-// Instruction descriptor of kind::f16: D f32, A and B half, both K-major, N = TN, M = 128.
-template <int TN>
+// Instruction descriptor of kind::f16: D f32, A and B half, M = 128, N = TN; mn: both operands
+// MN-major (bits 15 and 16), else both K-major.
+template <int TN, bool MN>
 __host__ __device__ constexpr uint32_t idesc()
 {
-    return (1u << 4) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    return (1u << 4) | (MN ? (1u << 15) | (1u << 16) : 0u) | ((uint32_t)(TN >> 3) << 17) |
+           ((uint32_t)(128 >> 4) << 24);
 }
 
 __device__ __forceinline__ unsigned long long global_ns()
@@ -117,6 +122,11 @@ __device__ __forceinline__ bool wait_or_fail(uint32_t mb, uint32_t parity, int *
     return false;
 }
 
+__device__ __forceinline__ void expect_tx(uint32_t mb, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mb), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
                                             uint32_t mbar)
 {
@@ -126,37 +136,51 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map
                  : "memory");
 }
 
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
-                                            uint32_t mbar)
+// Contiguous global -> shared copy (16-byte aligned ends, size a multiple of 16).
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar)
 {
-    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-                 "[%0], [%1, {%2, %3, %4}], [%5];"
-                 :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(mbar)
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(dst), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem, unsigned long long ad, unsigned long long bd, uint32_t id,
+                                        uint32_t acc)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                 :: "r"(tmem), "l"(ad), "l"(bd), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ void commit(uint32_t mb)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mb)
                  : "memory");
 }
 
-template <int TN>
-__global__ void __launch_bounds__(128)
-conv3_tma_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmw, int H, int W,
-                 int C, int cout, int ntn, int nstages, float alpha, float beta, float *y, int ldy, int vec_y,
-                 int *err)
+// 32 consecutive accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t r[32])
 {
-    extern __shared__ unsigned char dyn_raw[];
-    __shared__ __align__(8) unsigned long long full[kMaxStages], empty[kMaxStages], done;
-    __shared__ uint32_t tmem_holder;
-    __shared__ int failed;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                 "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+                 "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                   "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+                   "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+                   "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
 
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int x0 = blockIdx.x * kTilePx, y0 = blockIdx.y * kTileRows;
-    const int img = blockIdx.z / ntn, n0 = (blockIdx.z % ntn) * TN;
-    const int nchunks = C / kChunk;
-    constexpr int kSB = stage_bytes<TN>();
-    constexpr uint32_t kTx = 2 * kPlaneBytes + 18 * TN * 16;      // bytes the 3 loads of a stage bring
-    const uint32_t base = (smem_u32(dyn_raw) + 1023u) & ~1023u;   // 1 KB aligned stage 0
-
-    if (warp == 0) {
+// Shared prologue: TMEM allocation by warp 0, barrier initialisation by thread 32.
+template <uint32_t COLS>
+__device__ __forceinline__ uint32_t setup(uint32_t *tmem_holder, unsigned long long *full, unsigned long long *empty,
+                                          unsigned long long *done, int nstages, int *failed)
+{
+    const int tid = threadIdx.x;
+    if (tid < 32) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_u32(&tmem_holder)), "r"((uint32_t)TN));
+                     :: "r"(smem_u32(tmem_holder)), "r"(COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 32) {
@@ -164,31 +188,61 @@ conv3_tma_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant_
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&full[s])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&empty[s])));
         }
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&done)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(done)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        failed = 0;
+        *failed = 0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    const uint32_t tmem = tmem_holder;
+    return *tmem_holder;
+}
+
+template <uint32_t COLS>
+__device__ __forceinline__ void teardown(uint32_t tmem)
+{
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (threadIdx.x < 32)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(COLS));
+}
+
+// ---- forward -------------------------------------------------------------------------------
+// grid (tiles in x, tiles in y, N * output-channel blocks); wp points at this launch's packed
+// weights: block nb, chunk i is the 18 * TN * 8 halves at ((nb * nchunks + i) * 18 * TN * 8).
+template <int TN>
+__global__ void __launch_bounds__(128)
+conv3_tma_kernel(const __grid_constant__ CUtensorMap tmx, const __half *__restrict__ wp, int H, int W, int C,
+                 int cout, int ntn, int nstages, float alpha, float beta, float *y, int ldy, int vec_y, int *err)
+{
+    extern __shared__ unsigned char dyn_raw[];
+    __shared__ __align__(8) unsigned long long full[kFwdStages], empty[kFwdStages], done;
+    __shared__ uint32_t tmem_holder;
+    __shared__ int failed;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int x0 = blockIdx.x * kTilePx, y0 = blockIdx.y * kTileRows;
+    const int img = blockIdx.z / ntn, nb = blockIdx.z % ntn, n0 = nb * TN;
+    const int nchunks = C / kChunk;
+    constexpr int kSB = fwd_stage_bytes<TN>();
+    constexpr uint32_t kTx = 2 * kPlane + 18 * TN * 16;       // bytes the two copies of a stage bring
+    const uint32_t base = (smem_u32(dyn_raw) + 1023u) & ~1023u;
+
+    const uint32_t tmem = setup<TN>(&tmem_holder, full, empty, &done, nstages, &failed);
 
     if (warp == 0 && lane == 0) {
-        // producer
         asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&tmx)) : "memory");
-        asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&tmw)) : "memory");
+        const __half *wblk = wp + (size_t)nb * nchunks * 18 * TN * 8;
         for (int i = 0; i < nchunks; ++i) {
             const int s = i % nstages;
             if (i >= nstages && !wait_or_fail(smem_u32(&empty[s]), (uint32_t)((i / nstages - 1) & 1), &failed, err))
                 break;
             const uint32_t st = base + (uint32_t)(s * kSB), fb = smem_u32(&full[s]);
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(fb), "r"(kTx) : "memory");
-            tma_load_4d(st, &tmx, i * kChunk, x0 - 1, y0 - 1, img, fb);
-            tma_load_4d(st + kPlaneStride, &tmx, i * kChunk + 8, x0 - 1, y0 - 1, img, fb);
-            tma_load_3d(st + kASlab, &tmw, 0, n0, i * 18, fb);
+            expect_tx(fb, kTx);
+            tma_load_4d(st, &tmx, 8 * (x0 - 1), y0 - 1, 2 * i, img, fb);       // planes 2i, 2i + 1
+            bulk_load(st + kFwdA, wblk + (size_t)i * 18 * TN * 8, 18 * TN * 16, fb);
         }
     } else if (warp == 1 && lane == 0) {
-        // MMA issuer
         for (int i = 0; i < nchunks; ++i) {
             const int s = i % nstages;
             if (!wait_or_fail(smem_u32(&full[s]), (uint32_t)((i / nstages) & 1), &failed, err)) break;
@@ -197,20 +251,13 @@ conv3_tma_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant_
             #pragma unroll
             for (int t = 0; t < 9; ++t) {
                 const int ky = t / 3, kx = t % 3;
-                const unsigned long long ad = desc(st + (uint32_t)((ky * kHaloPx + kx) * 16), kPlaneStride,
-                                                   kHaloPx * 16);
-                const unsigned long long bd = desc(st + kASlab + (uint32_t)(2 * t * TN * 16), TN * 16, 128);
-                const uint32_t acc = (i > 0 || t > 0) ? 1u : 0u;
-                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-                             :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc<TN>()), "r"(acc));
+                mma_f16(tmem, desc(st + (uint32_t)((ky * kHaloPx + kx) * 16), kPlane, kHaloPx * 16),
+                        desc(st + kFwdA + (uint32_t)(2 * t * TN * 16), TN * 16, 128), idesc<TN, false>(),
+                        (i > 0 || t > 0) ? 1u : 0u);
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(smem_u32(&empty[s])) : "memory");
+            commit(smem_u32(&empty[s]));
         }
-        // covers every MMA this thread issued, also after a failure
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                     :: "r"(smem_u32(&done)) : "memory");
+        commit(smem_u32(&done));    // covers every MMA this thread issued, also after a failure
     }
     __syncwarp();
     wait_or_fail(smem_u32(&done), 0u, &failed, err);
@@ -225,17 +272,7 @@ conv3_tma_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant_
         #pragma unroll 1
         for (int c = 0; c < TN; c += 32) {
             uint32_t r[32];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c;
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                         "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-                         "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                           "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-                           "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-                           "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                         : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, r);
             if (!valid) continue;
             const int col0 = n0 + c;
             if (vec_y && col0 + 32 <= cout) {
@@ -261,23 +298,138 @@ conv3_tma_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant_
             }
         }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"((uint32_t)TN));
+    teardown<TN>(tmem);
 }
 
-// wp[((chunk * 9 + tap) * 2 + q) * cout * 8 + o * 8 + e] = w[o * 9C + tap * C + chunk * 16 + q * 8 + e]
-__global__ void pack3_kernel(const __half *__restrict__ w, int cout, int C, __half *__restrict__ wp)
+// ---- weight gradient -------------------------------------------------------------------------
+// grid (input-channel blocks of 128 x output-channel blocks of 32, pixel-tile splits).  A CTA
+// accumulates D_t[c][o] = sum over its pixel tiles of x(p + tap t)[c] dz(p)[o] for all nine taps
+// (9 x 32 TMEM columns), then adds alpha D_t into gw[o][t*C + c] with float32 atomics.
+__global__ void __launch_bounds__(128)
+conv3_wgrad_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmz, int H, int W,
+                   int C, int cout, int tiles_x, int tiles_y, int ntiles, int nbk, int per, int planes, int nstages,
+                   int stage_bytes, float alpha, float *gw, int ldg, int *err)
 {
-    const long long total = 9LL * C * cout;
+    extern __shared__ unsigned char dyn_raw[];
+    __shared__ __align__(8) unsigned long long full[kWgStages], empty[kWgStages], done;
+    __shared__ uint32_t tmem_holder;
+    __shared__ int failed;
+    constexpr uint32_t kCols = 512;         // 9 taps x 32 columns, rounded up to a power of two
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mb = blockIdx.x / nbk, nb = blockIdx.x % nbk;
+    const int t_beg = blockIdx.y * per;
+    const int t_end = min(ntiles, t_beg + per);
+    if (t_beg >= t_end) return;             // uniform over the CTA
+    const int a_bytes = (planes * kPlane + 127) / 128 * 128;
+    const uint32_t tx = (uint32_t)(planes * kPlane + 4 * kDzPlane);
+    const uint32_t base = (smem_u32(dyn_raw) + 1023u) & ~1023u;
+
+    const uint32_t tmem = setup<kCols>(&tmem_holder, full, empty, &done, nstages, &failed);
+    const int n_it = t_end - t_beg;
+
+    if (warp == 0 && lane == 0) {
+        asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&tmx)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&tmz)) : "memory");
+        for (int it = 0; it < n_it; ++it) {
+            const int s = it % nstages;
+            if (it >= nstages && !wait_or_fail(smem_u32(&empty[s]), (uint32_t)((it / nstages - 1) & 1), &failed, err))
+                break;
+            const int t = t_beg + it, per_img = tiles_x * tiles_y;
+            const int img = t / per_img, rem = t - img * per_img;
+            const int x0 = (rem % tiles_x) * kTilePx, y0 = (rem / tiles_x) * kTileRows;
+            const uint32_t st = base + (uint32_t)(s * stage_bytes), fb = smem_u32(&full[s]);
+            expect_tx(fb, tx);
+            tma_load_4d(st, &tmx, 8 * (x0 - 1), y0 - 1, kWgPlanes * mb, img, fb);
+            tma_load_4d(st + a_bytes, &tmz, 8 * x0, y0, 4 * nb, img, fb);
+        }
+    } else if (warp == 1 && lane == 0) {
+        for (int it = 0; it < n_it; ++it) {
+            const int s = it % nstages;
+            if (!wait_or_fail(smem_u32(&full[s]), (uint32_t)((it / nstages) & 1), &failed, err)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t st = base + (uint32_t)(s * stage_bytes);
+            #pragma unroll 1
+            for (int t = 0; t < 9; ++t) {
+                const int ky = t / 3, kx = t % 3;
+                #pragma unroll
+                for (int j = 0; j < kTileRows / 2; ++j) {        // K = 16 pixels: image rows 2j, 2j + 1
+                    mma_f16(tmem + (uint32_t)(t * kWgTN),
+                            desc(st + (uint32_t)(((2 * j + ky) * kHaloPx + kx) * 16), kHaloPx * 16, kPlane),
+                            desc(st + (uint32_t)a_bytes + (uint32_t)(2 * j * 128), 128, kDzPlane),
+                            idesc<kWgTN, true>(), (it > 0 || j > 0) ? 1u : 0u);
+                }
+            }
+            commit(smem_u32(&empty[s]));
+        }
+        commit(smem_u32(&done));
+    }
+    __syncwarp();
+    wait_or_fail(smem_u32(&done), 0u, &failed, err);
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+
+    if (!failed) {
+        const int c = kWgPlanes * 8 * mb + warp * 32 + lane;
+        #pragma unroll 1
+        for (int t = 0; t < 9; ++t) {
+            uint32_t r[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * kWgTN), r);
+            if (c >= C) continue;
+            float *g = gw + (size_t)t * C + c;
+            #pragma unroll
+            for (int j = 0; j < kWgTN; ++j) {
+                const int o = kWgTN * nb + j;
+                if (o < cout) atomicAdd(g + (size_t)o * ldg, alpha * __uint_as_float(r[j]));
+            }
+        }
+    }
+    teardown<kCols>(tmem);
+}
+
+// ---- layout kernels ------------------------------------------------------------------------
+// xb[((n * C/8 + g) * H + y) * W + x][e] = half(scale * x[n][y][x][8 g + e]); one thread per 8 channels.
+__global__ void to_half_blocked_kernel(const float *__restrict__ x, int N, int H, int W, int C, float scale,
+                                       __half *__restrict__ xb)
+{
+    const int G = C / 8;
+    const long long total = (long long)N * G * H * W;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int xx = (int)(i % W);
+        long long r = i / W;
+        const int yy = (int)(r % H);
+        r /= H;
+        const int g = (int)(r % G);
+        const int n = (int)(r / G);
+        const float4 *src = reinterpret_cast<const float4 *>(x + (((size_t)n * H + yy) * W + xx) * C + 8 * g);
+        const float4 a = src[0], b = src[1];
+        __half2 h0 = __floats2half2_rn(scale * a.x, scale * a.y), h1 = __floats2half2_rn(scale * a.z, scale * a.w);
+        __half2 h2 = __floats2half2_rn(scale * b.x, scale * b.y), h3 = __floats2half2_rn(scale * b.z, scale * b.w);
+        *reinterpret_cast<uint4 *>(xb + (size_t)i * 8) =
+            make_uint4(*reinterpret_cast<uint32_t *>(&h0), *reinterpret_cast<uint32_t *>(&h1),
+                       *reinterpret_cast<uint32_t *>(&h2), *reinterpret_cast<uint32_t *>(&h3));
+    }
+}
+
+// wp[(((nb * nchunks + chunk) * 18 + tap * 2 + q) * TN + r) * 8 + e] = w[nb*TN + r][tap*C + chunk*16 + q*8 + e]
+// (zero for output channels nb*TN + r >= cout).
+__global__ void pack3_kernel(const __half *__restrict__ w, int cout, int C, int TN, long long total,
+                             __half *__restrict__ wp)
+{
+    const int nchunks = C / kChunk;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
         const int e = (int)(i & 7);
-        const long long r = i >> 3;
-        const int o = (int)(r % cout);
-        const int kg = (int)(r / cout);              // (chunk * 9 + tap) * 2 + q
-        const int q = kg & 1, ct = kg >> 1, tap = ct % 9, chunk = ct / 9;
-        wp[i] = w[(size_t)o * 9 * C + (size_t)tap * C + chunk * kChunk + q * 8 + e];
+        long long r = i >> 3;
+        const int row = (int)(r % TN);
+        r /= TN;
+        const int kg = (int)(r % 18);
+        r /= 18;
+        const int chunk = (int)(r % nchunks);
+        const int nb = (int)(r / nchunks);
+        const int o = nb * TN + row, tap = kg >> 1, q = kg & 1;
+        wp[i] = o < cout ? w[(size_t)o * 9 * C + (size_t)tap * C + chunk * kChunk + q * 8 + e] : __float2half(0.0f);
     }
 }
 
@@ -310,88 +462,162 @@ EncodeTiledFn encode_tiled()
     return fn;
 }
 
+// Tensor map of a blocked half activation [N][C/8][H][W][8] as the 4-D view (8W, H, C/8, N) with
+// the box {box_px * 8, box_rows, box_planes, 1}.
+CUresult blocked_map(CUtensorMap *map, const void *xb, int N, int H, int W, int C, int box_px, int box_rows,
+                     int box_planes)
+{
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return CUDA_ERROR_NOT_SUPPORTED;
+    const cuuint64_t dim[4] = {8ull * W, (cuuint64_t)H, (cuuint64_t)(C / 8), (cuuint64_t)N};
+    const cuuint64_t str[3] = {16ull * W, 16ull * W * H, 2ull * W * H * C};
+    const cuuint32_t box[4] = {(cuuint32_t)(8 * box_px), (cuuint32_t)box_rows, (cuuint32_t)box_planes, 1};
+    const cuuint32_t ones[4] = {1, 1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, const_cast<void *>(xb), dim, str, box, ones,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+}
+
+bool blocked_args_ok(const void *p, int N, int H, int W, int C)
+{
+    return p && N >= 1 && H >= 1 && W >= 1 && C >= 8 && C % 8 == 0 && (reinterpret_cast<uintptr_t>(p) & 15) == 0 &&
+           (long long)N * H * W * C <= (1LL << 40) && (long long)W * 8 <= 0xffffffffLL;
+}
+
 template <int TN>
-cudaError_t launch_conv3_tma(const CUtensorMap &tmx, const CUtensorMap &tmw, int N, int H, int W, int C, int cout,
+cudaError_t launch_conv3_tma(const CUtensorMap &tmx, const __half *wp, int N, int H, int W, int C, int cout,
                              float alpha, float beta, float *y, int ldy, int *err, cudaStream_t s)
 {
     const int ntn = (cout + TN - 1) / TN;
     const int nchunks = C / kChunk;
-    const int nstages = nchunks < kMaxStages ? nchunks : kMaxStages;
+    const int nstages = nchunks < kFwdStages ? nchunks : kFwdStages;
     // shared memory also caps the CTAs per SM so that their accumulators fit in the 512 TMEM
     // columns: with 128 columns each, at most 4 CTAs may be resident, so reserve >= 2 stages
     const int reserve = (TN == 128 && nstages < 2) ? 2 : nstages;
-    const size_t smem = (size_t)reserve * stage_bytes<TN>() + 1024;
+    const size_t smem = (size_t)reserve * fwd_stage_bytes<TN>() + 1024;
     dim3 grid((W + kTilePx - 1) / kTilePx, (H + kTileRows - 1) / kTileRows, N * ntn);
     const int vec_y = (ldy % 4 == 0) && ((reinterpret_cast<uintptr_t>(y) & 15) == 0);
     static bool attr_set = false;       // per instantiation
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(conv3_tma_kernel<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(kMaxStages * stage_bytes<TN>() + 1024));
+                                             (int)(kFwdStages * fwd_stage_bytes<TN>() + 1024));
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    conv3_tma_kernel<TN><<<grid, 128, smem, s>>>(tmx, tmw, H, W, C, cout, ntn, nstages, alpha, beta, y, ldy, vec_y,
+    conv3_tma_kernel<TN><<<grid, 128, smem, s>>>(tmx, wp, H, W, C, cout, ntn, nstages, alpha, beta, y, ldy, vec_y,
                                                  err);
     return cudaGetLastError();
 }
 
 } // namespace
 
+extern "C" long long smrt_nn_pack3_halves(int cout, int C)
+{
+    if (cout < 1 || C < kChunk || C % kChunk != 0) return -1;
+    const int TN = tile_n(cout);
+    return 9LL * C * ((cout + TN - 1) / TN) * TN;
+}
+
 extern "C" int smrt_nn_pack3(const void *w, int cout, int C, void *wp, void *stream)
 {
-    if (!w || !wp || cout < 1 || C < kChunk || C % kChunk != 0 || 9LL * C * cout > 0x7fffffffLL)
-        return tma_fail(SMRT_ERR_ARG, "smrt_nn_pack3: bad arguments (cout %d C %d; C must be a multiple of 16)", cout,
-                        C);
-    const long long total = 9LL * C * cout;
+    const long long total = smrt_nn_pack3_halves(cout, C);
+    if (!w || !wp || total < 0 || total > 0x7fffffffLL || (reinterpret_cast<uintptr_t>(wp) & 15) != 0)
+        return tma_fail(SMRT_ERR_ARG, "smrt_nn_pack3: bad arguments (cout %d C %d; C must be a multiple of 16, wp "
+                        "16-byte aligned)", cout, C);
     const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
-    pack3_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>((const __half *)w, cout, C, (__half *)wp);
+    pack3_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>((const __half *)w, cout, C, tile_n(cout), total,
+                                                           (__half *)wp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return tma_fail(SMRT_ERR_CUDA, "smrt_nn_pack3: %s", cudaGetErrorString(e));
     return SMRT_OK;
 }
 
-extern "C" int smrt_nn_conv3_tma(const void *xh, int N, int H, int W, int C, const void *wp, int cout, float alpha,
+extern "C" int smrt_nn_to_half_blocked(const float *x, int N, int H, int W, int C, float scale, void *xb,
+                                       void *stream)
+{
+    if (!x || !blocked_args_ok(xb, N, H, W, C) || (reinterpret_cast<uintptr_t>(x) & 15) != 0)
+        return tma_fail(SMRT_ERR_ARG, "smrt_nn_to_half_blocked: bad arguments (N %d H %d W %d C %d; C must be a "
+                        "multiple of 8, x and xb 16-byte aligned)", N, H, W, C);
+    const long long total = (long long)N * (C / 8) * H * W;
+    const int blocks = (int)((total + 255) / 256 < 8192 ? (total + 255) / 256 : 8192);
+    to_half_blocked_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(x, N, H, W, C, scale, (__half *)xb);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return tma_fail(SMRT_ERR_CUDA, "smrt_nn_to_half_blocked: %s", cudaGetErrorString(e));
+    return SMRT_OK;
+}
+
+extern "C" int smrt_nn_conv3_tma(const void *xb, int N, int H, int W, int C, const void *wp, int cout, float alpha,
                                  float beta, float *y, int ldy, int *err, void *stream)
 {
-    if (!xh || !wp || !y || N < 1 || H < 1 || W < 1 || C < kChunk || C % kChunk != 0 || cout < 1 || ldy < cout ||
-        (reinterpret_cast<uintptr_t>(xh) & 15) != 0 || (reinterpret_cast<uintptr_t>(wp) & 15) != 0 ||
-        (H + kTileRows - 1) / kTileRows > 65535 || (long long)N * H * W * C > (1LL << 40) || 9LL * C > 0x7fffffffLL)
+    if (!blocked_args_ok(xb, N, H, W, C) || C % kChunk != 0 || !wp || !y || cout < 1 || ldy < cout ||
+        (reinterpret_cast<uintptr_t>(wp) & 15) != 0 || (H + kTileRows - 1) / kTileRows > 65535 ||
+        (long long)N * ((cout + tile_n(cout) - 1) / tile_n(cout)) > 65535)
         return tma_fail(SMRT_ERR_ARG,
                         "smrt_nn_conv3_tma: bad arguments (N %d H %d W %d C %d cout %d ldy %d; C must be a multiple "
-                        "of 16, xh and wp 16-byte aligned)", N, H, W, C, cout, ldy);
-    const int TN = cout <= 32 ? 32 : cout <= 64 ? 64 : 128;
-    if ((long long)N * ((cout + TN - 1) / TN) > 65535)
-        return tma_fail(SMRT_ERR_ARG, "smrt_nn_conv3_tma: N x output-channel tiles exceeds the grid (N %d cout %d)", N,
-                        cout);
-    EncodeTiledFn enc = encode_tiled();
-    if (!enc) return tma_fail(SMRT_ERR_CUDA, "smrt_nn_conv3_tma: cuTensorMapEncodeTiled is not available");
-
-    // activations: (C, W, H, N) halves, box 8 channels x 10 pixels x 18 rows x 1 image
-    CUtensorMap tmx, tmw;
-    const cuuint64_t xdim[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
-    const cuuint64_t xstr[3] = {2ull * C, 2ull * C * W, 2ull * C * W * H};
-    const cuuint32_t xbox[4] = {8, (cuuint32_t)kHaloPx, (cuuint32_t)kHaloRows, 1};
-    const cuuint32_t ones[4] = {1, 1, 1, 1};
-    CUresult r = enc(&tmx, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, const_cast<void *>(xh), xdim, xstr, xbox, ones,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS)
-        return tma_fail(SMRT_ERR_CUDA, "smrt_nn_conv3_tma: activation tensor map rejected (%d)", (int)r);
-    // packed weights: (8, cout, 9C/8) halves, box 8 x TN x 18 (all nine taps of one 16-channel chunk)
-    const cuuint64_t wdim[3] = {8, (cuuint64_t)cout, (cuuint64_t)(9 * C / 8)};
-    const cuuint64_t wstr[2] = {16, 16ull * cout};
-    const cuuint32_t wbox[3] = {8, (cuuint32_t)TN, 18};
-    r = enc(&tmw, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void *>(wp), wdim, wstr, wbox, ones,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS)
-        return tma_fail(SMRT_ERR_CUDA, "smrt_nn_conv3_tma: weight tensor map rejected (%d)", (int)r);
-
+                        "of 16, xb and wp 16-byte aligned)", N, H, W, C, cout, ldy);
+    CUtensorMap tmx;
+    CUresult r = blocked_map(&tmx, xb, N, H, W, C, kHaloPx, kHaloRows, 2);
+    if (r != CUDA_SUCCESS) return tma_fail(SMRT_ERR_CUDA, "smrt_nn_conv3_tma: tensor map rejected (%d)", (int)r);
     cudaStream_t s = (cudaStream_t)stream;
+    const __half *w = (const __half *)wp;
     cudaError_t e;
-    if (TN == 32) e = launch_conv3_tma<32>(tmx, tmw, N, H, W, C, cout, alpha, beta, y, ldy, err, s);
-    else if (TN == 64) e = launch_conv3_tma<64>(tmx, tmw, N, H, W, C, cout, alpha, beta, y, ldy, err, s);
-    else e = launch_conv3_tma<128>(tmx, tmw, N, H, W, C, cout, alpha, beta, y, ldy, err, s);
+    const int TN = tile_n(cout);
+    if (TN == 32) e = launch_conv3_tma<32>(tmx, w, N, H, W, C, cout, alpha, beta, y, ldy, err, s);
+    else if (TN == 64) e = launch_conv3_tma<64>(tmx, w, N, H, W, C, cout, alpha, beta, y, ldy, err, s);
+    else e = launch_conv3_tma<128>(tmx, w, N, H, W, C, cout, alpha, beta, y, ldy, err, s);
     if (e != cudaSuccess) return tma_fail(SMRT_ERR_CUDA, "smrt_nn_conv3_tma: %s", cudaGetErrorString(e));
+    return SMRT_OK;
+}
+
+extern "C" int smrt_nn_conv3_wgrad_tma(const void *xb, int N, int H, int W, int C, const void *dzb, int cout,
+                                       float alpha, float *gw, int ldg, int *err, void *stream)
+{
+    if (!blocked_args_ok(xb, N, H, W, C) || !blocked_args_ok(dzb, N, H, W, cout) || !gw || ldg < 9 * C)
+        return tma_fail(SMRT_ERR_ARG,
+                        "smrt_nn_conv3_wgrad_tma: bad arguments (N %d H %d W %d C %d cout %d ldg %d; C and cout must "
+                        "be multiples of 8, xb and dzb 16-byte aligned)", N, H, W, C, cout, ldg);
+    const int tiles_x = (W + kTilePx - 1) / kTilePx, tiles_y = (H + kTileRows - 1) / kTileRows;
+    const long long ntiles = (long long)N * tiles_x * tiles_y;
+    if (ntiles > 0x7fffffffLL) return tma_fail(SMRT_ERR_ARG, "smrt_nn_conv3_wgrad_tma: too many pixels");
+    const int planes = C / 8 < kWgPlanes ? C / 8 : kWgPlanes;
+    CUtensorMap tmx, tmz;
+    CUresult r = blocked_map(&tmx, xb, N, H, W, C, kHaloPx, kHaloRows, planes);
+    if (r == CUDA_SUCCESS) r = blocked_map(&tmz, dzb, N, H, W, cout, kTilePx, kTileRows, 4);
+    if (r != CUDA_SUCCESS)
+        return tma_fail(SMRT_ERR_CUDA, "smrt_nn_conv3_wgrad_tma: tensor map rejected (%d)", (int)r);
+
+    const int mbk = (C + 8 * kWgPlanes - 1) / (8 * kWgPlanes), nbk = (cout + kWgTN - 1) / kWgTN;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 148;
+    // one CTA per SM (each holds all 512 TMEM columns): split the pixel tiles to fill the SMs
+    long long splits = sms / (mbk * nbk);
+    if (splits < 1) splits = 1;
+    if (splits > ntiles) splits = ntiles;
+    const int per = (int)((ntiles + splits - 1) / splits);
+    splits = (ntiles + per - 1) / per;
+    const int a_bytes = (planes * kPlane + 127) / 128 * 128;
+    const int stage = (a_bytes + 4 * kDzPlane + 1023) / 1024 * 1024;
+    const int a_reach = kWgPlanes * kPlane;         // the MMA's 128 rows read 16 planes from a stage start
+    int nstages = kWgStages;
+    auto need = [&](int n) { return (size_t)(n - 1) * stage + (size_t)(stage > a_reach ? stage : a_reach + 128); };
+    while (nstages > 2 && need(nstages) + 1024 > 220 * 1024) --nstages;
+    size_t smem = need(nstages) + 1024;
+    if (smem < 120 * 1024) smem = 120 * 1024;       // keeps a second CTA (and its TMEM request) off the SM
+    if (smem > 220 * 1024 || mbk * nbk > 65535 || splits > 65535)
+        return tma_fail(SMRT_ERR_ARG, "smrt_nn_conv3_wgrad_tma: sizes out of range (C %d cout %d)", C, cout);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(conv3_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             220 * 1024);
+        if (e != cudaSuccess) return tma_fail(SMRT_ERR_CUDA, "smrt_nn_conv3_wgrad_tma: %s", cudaGetErrorString(e));
+        attr_set = true;
+    }
+    dim3 grid(mbk * nbk, (unsigned)splits);
+    conv3_wgrad_kernel<<<grid, 128, smem, (cudaStream_t)stream>>>(tmx, tmz, H, W, C, cout, tiles_x, tiles_y,
+                                                                  (int)ntiles, nbk, per, planes, nstages, stage, alpha,
+                                                                  gw, ldg, err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return tma_fail(SMRT_ERR_CUDA, "smrt_nn_conv3_wgrad_tma: %s", cudaGetErrorString(e));
     return SMRT_OK;
 }

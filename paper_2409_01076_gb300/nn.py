@@ -44,16 +44,33 @@ def smrt_nn_conv3_tc(x, w, y, alpha=1.0, beta=0.0, err=None):
                                         int(y.shape[-1]), _p(err), _s()))
 
 
-def smrt_nn_conv3_tma(xh, wp, y, cout, alpha=1.0, beta=0.0, err=None):
-    """xh: (N, H, W, C) half; wp: 9*C*cout halves from smrt_nn_pack3; y: N*H*W rows of cout float32."""
-    n, h, wd, c = xh.shape
-    _check(_lib.load().smrt_nn_conv3_tma(_p(xh), n, h, wd, c, _p(wp), int(cout), float(alpha), float(beta), _p(y),
-                                         int(y.shape[-1]), _p(err), _s()))
+def smrt_nn_to_half_blocked(x, xb, scale=1.0):
+    """x: (N, H, W, C) float32; xb: N*C*H*W halves, written as [N][C/8][H][W][8]."""
+    n, h, w, c = x.shape
+    _check(_lib.load().smrt_nn_to_half_blocked(_p(x), n, h, w, c, float(scale), _p(xb), _s()))
+
+
+def smrt_nn_pack3_halves(cout, C):
+    return int(_lib.load().smrt_nn_pack3_halves(int(cout), int(C)))
 
 
 def smrt_nn_pack3(w, C, wp):
-    """w: (cout, 9C) half; wp: 9*C*cout halves (any shape)."""
+    """w: (cout, 9C) half; wp: smrt_nn_pack3_halves(cout, C) halves (any shape)."""
     _check(_lib.load().smrt_nn_pack3(_p(w), int(w.shape[0]), int(C), _p(wp), _s()))
+
+
+def smrt_nn_conv3_tma(xb, nhwc, wp, y, cout, alpha=1.0, beta=0.0, err=None):
+    """xb: blocked half activations of shape nhwc = (N, H, W, C); y: N*H*W rows of cout float32."""
+    n, h, w, c = nhwc
+    _check(_lib.load().smrt_nn_conv3_tma(_p(xb), int(n), int(h), int(w), int(c), _p(wp), int(cout), float(alpha),
+                                         float(beta), _p(y), int(y.shape[-1]), _p(err), _s()))
+
+
+def smrt_nn_conv3_wgrad_tma(xb, nhwc, dzb, cout, gw, alpha=1.0, err=None):
+    """gw (cout, ldg >= 9C) float32 += alpha * weight gradient from blocked half x and dz."""
+    n, h, w, c = nhwc
+    _check(_lib.load().smrt_nn_conv3_wgrad_tma(_p(xb), int(n), int(h), int(w), int(c), _p(dzb), int(cout),
+                                               float(alpha), _p(gw), int(gw.shape[-1]), _p(err), _s()))
 
 
 def smrt_nn_im2col3(x, col):

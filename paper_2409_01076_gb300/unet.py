@@ -115,14 +115,14 @@ class UNet:
             K.smrt_nn_to_half(w, h)
             self._wh[name] = h
             if self._tma(k, ci):                # packed for the TMA convolution
-                self._wp[name] = t.empty(9 * ci * co, dtype=t.float16, device=self.device)
+                self._wp[name] = t.empty(K.smrt_nn_pack3_halves(co, ci), dtype=t.float16, device=self.device)
                 K.smrt_nn_pack3(h, ci, self._wp[name])
             if k == 3 and name != "enc1a":      # weights of the adjoint convolution (input gradient)
                 f = t.empty((ci, 9 * co), dtype=t.float16, device=self.device)
                 K.smrt_nn_flip3(w, f)
                 self._wf[name] = f
                 if self._tma(k, co):
-                    self._wfp[name] = t.empty(9 * ci * co, dtype=t.float16, device=self.device)
+                    self._wfp[name] = t.empty(K.smrt_nn_pack3_halves(ci, co), dtype=t.float16, device=self.device)
                     K.smrt_nn_pack3(f, co, self._wfp[name])
 
     def _conv(self, spec, x, cache):
@@ -132,11 +132,12 @@ class UNet:
         rows = n * h * w
         kk = k * k * ci
         y = t.empty((n, h, w, co), dtype=t.float32, device=self.device)
+        xb = None
         if self._tma(k, ci):
-            # operands by TMA: half activations, nine taps as shifted views of one haloed tile
-            xh = t.empty((n, h, w, ci), dtype=t.float16, device=self.device)
-            K.smrt_nn_to_half(x, xh)
-            K.smrt_nn_conv3_tma(xh, self._wp[name], y, co, 1.0, 0.0, self._gemm_err)
+            # operands by TMA: blocked half activations, nine taps as shifted views of one haloed tile
+            xb = t.empty(n * h * w * ci, dtype=t.float16, device=self.device)
+            K.smrt_nn_to_half_blocked(x, xb)
+            K.smrt_nn_conv3_tma(xb, (n, h, w, ci), self._wp[name], y, co, 1.0, 0.0, self._gemm_err)
             col = None
         elif self._implicit(k, ci):
             # implicit GEMM: the A tiles are gathered from x, no im2col matrix is built
@@ -153,7 +154,7 @@ class UNet:
         z = t.empty_like(y) if (act and cache is not None) else None
         K.smrt_nn_bias_act(y, self.params[name + ".b"], act, z, y)
         if cache is not None:
-            cache[name] = (col, z, x)
+            cache[name] = (col, z, x, xb)
         return y
 
     def _implicit(self, k, c):
@@ -167,35 +168,54 @@ class UNet:
     def _conv_bwd(self, spec, da, cache, need_dx=True):
         t = self.torch
         name, ci, co, k, act = spec
-        col, z, x = cache[name]
+        col, z, x, xb = cache[name]
         xshape = x.shape
         n, h, w, _ = xshape
         rows = n * h * w
         kk = k * k * ci
-        if col is None:             # the forward gathered from x; the weight gradient needs the matrix
-            col = t.empty((rows, _pad8(kk)), dtype=t.float16, device=self.device)
-            K.smrt_nn_im2col3(x, col)
-        ldk, ldz = col.shape[1], _pad8(co)
+        ldz = _pad8(co)
         dz = t.empty_like(da)
         K.smrt_nn_bias_act_bwd(da, z, act, dz, self.grads[name + ".b"])
-        dzh = t.empty((rows, ldz), dtype=t.float16, device=self.device)
-        K.smrt_nn_to_half_rows(dz.view(rows, co), dzh)
-        split = max(1, min(256, rows // 8192))
         gw = self.grads[name + ".w"]
-        if self.gemm_backend == "tcgen05":
-            # dW^T = col^T dz: the 9 cin dimension on the tensor core's M = 128 side, stored transposed
-            K.smrt_nn_gemm_tc(1, 2, kk, co, rows, 1.0, col, ldk, dzh, ldz, 1.0, gw, kk, split, self._gemm_err)
+        dzb = dzh = None
+
+        def blocked_dz():
+            d = t.empty(rows * co, dtype=t.float16, device=self.device)
+            K.smrt_nn_to_half_blocked(dz, d)
+            return d
+
+        def half_dz():
+            d = t.empty((rows, ldz), dtype=t.float16, device=self.device)
+            K.smrt_nn_to_half_rows(dz.view(rows, co), d)
+            return d
+
+        if xb is not None and co % 8 == 0:
+            # TMA weight gradient from the blocked halves of x (kept by the forward) and of dz
+            dzb = blocked_dz()
+            K.smrt_nn_conv3_wgrad_tma(xb, (n, h, w, ci), dzb, co, gw, 1.0, self._gemm_err)
         else:
-            self._gemm(1, 0, co, kk, rows, 1.0, dzh, ldz, col, ldk, 1.0, gw, kk, split)
+            if col is None:         # the forward gathered from x; the weight gradient needs the matrix
+                col = t.empty((rows, _pad8(kk)), dtype=t.float16, device=self.device)
+                K.smrt_nn_im2col3(x, col)
+            ldk = col.shape[1]
+            dzh = half_dz()
+            split = max(1, min(256, rows // 8192))
+            if self.gemm_backend == "tcgen05":
+                # dW^T = col^T dz: the 9 cin dimension on the tensor core's M = 128 side, stored transposed
+                K.smrt_nn_gemm_tc(1, 2, kk, co, rows, 1.0, col, ldk, dzh, ldz, 1.0, gw, kk, split, self._gemm_err)
+            else:
+                self._gemm(1, 0, co, kk, rows, 1.0, dzh, ldz, col, ldk, 1.0, gw, kk, split)
         if not need_dx:
             return None
         dx = t.empty(xshape, dtype=t.float32, device=self.device)
         if k == 1:
+            dzh = half_dz() if dzh is None else dzh
             self._gemm(0, 0, rows, ci, co, 1.0, dzh, ldz, self._wh[name], ci, 0.0, dx, ci)
             return dx
-        # dx = im2col(dz) * flip(W)^T: the adjoint 3x3 convolution, no col2im
+        # dx = conv3(dz, flip(W)): the adjoint 3x3 convolution, no col2im
         if self._tma(k, co):
-            K.smrt_nn_conv3_tma(dzh.view(n, h, w, co), self._wfp[name], dx, ci, 1.0, 0.0, self._gemm_err)
+            dzb = blocked_dz() if dzb is None else dzb
+            K.smrt_nn_conv3_tma(dzb, (n, h, w, co), self._wfp[name], dx, ci, 1.0, 0.0, self._gemm_err)
             return dx
         if self._implicit(k, co):
             K.smrt_nn_conv3_tc(dz.view(n, h, w, co), self._wf[name], dx, 1.0, 0.0, self._gemm_err)

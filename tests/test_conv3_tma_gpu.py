@@ -1,6 +1,7 @@
-"""smrt_nn_conv3_tma (TMA-fed operands, nine taps as shifted views of one zero-padded input tile)
-against an FP64 product of the same half operands, and against smrt_nn_conv3_tc; smrt_nn_pack3's
-layout element by element."""
+"""TMA-fed 3x3 convolutions (operands by cp.async.bulk.tensor / cp.async.bulk, nine taps as shifted
+views of one zero-padded input tile): the blocked half layout and the weight packing element by
+element; smrt_nn_conv3_tma and smrt_nn_conv3_wgrad_tma against FP64 products of the same half
+operands (numpy), and against the thread-gathered kernel smrt_nn_conv3_tc."""
 import numpy as np
 import pytest
 
@@ -14,20 +15,42 @@ def _rng(seed):
     return np.random.Generator(np.random.PCG64(seed))
 
 
-def test_pack3_layout():
+def _blocked(x):
+    """(N, H, W, C) -> flat [N][C/8][H][W][8], the layout the kernels read."""
+    n, h, w, c = x.shape
+    return np.ascontiguousarray(x.reshape(n, h, w, c // 8, 8).transpose(0, 3, 1, 2, 4)).ravel()
+
+
+def test_to_half_blocked_layout():
     import torch
-    cout, C = 5, 32
+    x = _rng(3).normal(size=(2, 5, 7, 24)).astype(np.float32)
+    xb = torch.empty(x.size, dtype=torch.float16, device="cuda")
+    S.smrt_nn_to_half_blocked(torch.tensor(x, device="cuda"), xb, 0.5)
+    torch.cuda.synchronize()
+    assert np.array_equal(xb.cpu().numpy(), _blocked((0.5 * x).astype(np.float16)))
+
+
+@pytest.mark.parametrize("cout,C", [(5, 32), (48, 16), (130, 32)])
+def test_pack3_layout(cout, C):
+    import torch
     w = _rng(1).normal(size=(cout, 9 * C)).astype(np.float16)
-    wp = torch.empty(9 * C * cout, dtype=torch.float16, device="cuda")
+    size = S.smrt_nn_pack3_halves(cout, C)
+    TN = 32 if cout <= 32 else 64 if cout <= 64 else 128
+    ntn = (cout + TN - 1) // TN
+    assert size == 9 * C * ntn * TN
+    wp = torch.empty(size, dtype=torch.float16, device="cuda")
     S.smrt_nn_pack3(torch.tensor(w, device="cuda"), C, wp)
     torch.cuda.synchronize()
-    got = wp.cpu().numpy().reshape(9 * C // 8, cout, 8)
-    for chunk in range(C // 16):
-        for tap in range(9):
-            for q in range(2):
-                kg = (chunk * 9 + tap) * 2 + q
-                c0 = tap * C + chunk * 16 + q * 8
-                assert np.array_equal(got[kg], w[:, c0:c0 + 8]), (chunk, tap, q)
+    got = wp.cpu().numpy().reshape(ntn, C // 16, 18, TN, 8)
+    for nb in range(ntn):
+        for chunk in range(C // 16):
+            for tap in range(9):
+                for q in range(2):
+                    c0 = tap * C + chunk * 16 + q * 8
+                    rows = w[nb * TN:(nb + 1) * TN, c0:c0 + 8]
+                    blk = got[nb, chunk, tap * 2 + q]
+                    assert np.array_equal(blk[:rows.shape[0]], rows), (nb, chunk, tap, q)
+                    assert not blk[rows.shape[0]:].any()
 
 
 def _conv(n, h, w, C, cout, alpha, beta, seed):
@@ -36,16 +59,16 @@ def _conv(n, h, w, C, cout, alpha, beta, seed):
     x = r.normal(size=(n, h, w, C)).astype(np.float16)
     wt = r.normal(size=(cout, 9 * C)).astype(np.float16)
     y0 = r.normal(size=(n * h * w, cout)).astype(np.float32)
-    xd = torch.tensor(x, device="cuda")
+    xb = torch.tensor(_blocked(x), device="cuda")
     wd = torch.tensor(wt, device="cuda")
-    wp = torch.empty(9 * C * cout, dtype=torch.float16, device="cuda")
+    wp = torch.empty(S.smrt_nn_pack3_halves(cout, C), dtype=torch.float16, device="cuda")
     S.smrt_nn_pack3(wd, C, wp)
     y = torch.tensor(y0, device="cuda")
     err = torch.zeros(1, dtype=torch.int32, device="cuda")
-    S.smrt_nn_conv3_tma(xd, wp, y, cout, alpha, beta, err)
+    S.smrt_nn_conv3_tma(xb, (n, h, w, C), wp, y, cout, alpha, beta, err)
     torch.cuda.synchronize()
     exp = alpha * U.im2col3(x.astype(np.float64)) @ wt.astype(np.float64).T + beta * y0
-    return y.cpu().numpy(), exp, int(err.item()), (xd, wd, y0)
+    return y.cpu().numpy(), exp, int(err.item()), (x, wd)
 
 
 @pytest.mark.parametrize("n,h,w,C,cout", [
@@ -74,28 +97,63 @@ def test_conv3_tma_agrees_with_the_gather_kernel():
     equal up to float32 accumulation order."""
     import torch
     n, h, w, C, cout = 2, 64, 48, 64, 96
-    got, _, err, (xd, wd, y0) = _conv(n, h, w, C, cout, 1.0, 0.0, seed=5)
+    got, _, err, (x, wd) = _conv(n, h, w, C, cout, 1.0, 0.0, seed=5)
     ref = torch.zeros((n * h * w, cout), device="cuda")
     e2 = torch.zeros(1, dtype=torch.int32, device="cuda")
-    S.smrt_nn_conv3_tc(xd.float(), wd, ref, 1.0, 0.0, e2)
+    S.smrt_nn_conv3_tc(torch.tensor(x.astype(np.float32), device="cuda"), wd, ref, 1.0, 0.0, e2)
     torch.cuda.synchronize()
     assert err == 0 and int(e2.item()) == 0
     ref = ref.cpu().numpy()
     assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
 
 
-def test_conv3_tma_rejects_unsupported_arguments():
+def _wgrad(n, h, w, C, cout, alpha, seed):
     import torch
-    xh = torch.zeros((1, 4, 4, 24), dtype=torch.float16, device="cuda")     # C % 16 != 0
-    wp = torch.zeros(9 * 24 * 8, dtype=torch.float16, device="cuda")
+    r = _rng(seed)
+    x = r.normal(size=(n, h, w, C)).astype(np.float16)
+    dz = r.normal(size=(n, h, w, cout)).astype(np.float16)
+    g0 = r.normal(size=(cout, 9 * C)).astype(np.float32)
+    gw = torch.tensor(g0, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    S.smrt_nn_conv3_wgrad_tma(torch.tensor(_blocked(x), device="cuda"), (n, h, w, C),
+                              torch.tensor(_blocked(dz), device="cuda"), cout, gw, alpha, err)
+    torch.cuda.synchronize()
+    exp = g0 + alpha * dz.astype(np.float64).reshape(-1, cout).T @ U.im2col3(x.astype(np.float64))
+    return gw.cpu().numpy(), exp, int(err.item())
+
+
+@pytest.mark.parametrize("n,h,w,C,cout", [
+    (2, 37, 21, 16, 24),      # ragged tiles, 2 of 16 channel planes (the MMA's other rows unused)
+    (1, 32, 40, 32, 32),      # the top U-Net level's shape
+    (1, 20, 12, 136, 40),     # two input-channel blocks (the second holds one plane), two output blocks
+    (3, 5, 3, 8, 8),          # images smaller than the tile and the halo box
+    (4, 64, 64, 96, 32),      # 128 pixel tiles split over the SMs, atomics from many blocks
+    (4, 128, 256, 16, 32),    # 1,024 tiles: several per block, every pipeline stage reused
+])
+def test_conv3_wgrad_tma_matches_fp64_product_of_the_same_halves(n, h, w, C, cout):
+    got, exp, err = _wgrad(n, h, w, C, cout, 0.5, seed=C + 7 * cout)
+    assert err == 0
+    d = np.abs(got - exp).max() / np.abs(exp).max()
+    assert d <= 1e-4, d
+
+
+def test_tma_kernels_reject_unsupported_arguments():
+    import torch
     y = torch.zeros((16, 8), device="cuda")
-    with pytest.raises(S.SmrtError) as ei:
-        S.smrt_nn_conv3_tma(xh, wp, y, 8)
+    wp = torch.zeros(9 * 24 * 32, dtype=torch.float16, device="cuda")
+    xb = torch.zeros(16 * 24, dtype=torch.float16, device="cuda")
+    with pytest.raises(S.SmrtError) as ei:                   # C % 16 != 0
+        S.smrt_nn_conv3_tma(xb, (1, 4, 4, 24), wp, y, 8)
     assert ei.value.status == S.SMRT_ERR_ARG
-    xm = torch.zeros(16 * 16 + 1, dtype=torch.float16, device="cuda")[1:].view(1, 4, 4, 16)   # misaligned
+    xm = torch.zeros(16 * 16 + 1, dtype=torch.float16, device="cuda")[1:]       # misaligned
     with pytest.raises(S.SmrtError) as ei:
-        S.smrt_nn_conv3_tma(xm, wp, y, 8)
+        S.smrt_nn_conv3_tma(xm, (1, 4, 4, 16), wp, y, 8)
     assert ei.value.status == S.SMRT_ERR_ARG
     with pytest.raises(S.SmrtError) as ei:
         S.smrt_nn_pack3(torch.zeros((8, 9 * 24), dtype=torch.float16, device="cuda"), 24, wp)
     assert ei.value.status == S.SMRT_ERR_ARG
+    gw = torch.zeros((12, 9 * 16), device="cuda")
+    with pytest.raises(S.SmrtError) as ei:                   # cout % 8 != 0
+        S.smrt_nn_conv3_wgrad_tma(xb, (1, 4, 4, 16), xb, 12, gw)
+    assert ei.value.status == S.SMRT_ERR_ARG
+    assert S.smrt_nn_pack3_halves(8, 24) == -1
