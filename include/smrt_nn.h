@@ -138,6 +138,30 @@ SMRT_API int smrt_nn_bias_act(const float *x, const float *bias, long long rows,
 SMRT_API int smrt_nn_bias_act_bwd(const float *da, const float *z, long long rows, int C, int act, float *dz,
                                   float *db, void *stream);
 
+/* Fused forms for the TMA convolutions (blocked half layout [N][C/8][H][W][8] as above); each
+ * float32 / half output pointer may be NULL to skip that output.  C % 8 == 0 where blocked output is
+ * written; all pointers 16-byte aligned; fewer than 2^31 elements.  The float32 results equal those
+ * of the plain kernels element for element.
+ *
+ * smrt_nn_bias_act_blocked: z = x + bias, a = SiLU(z) (or z), ab = half(a) blocked, for x (N,H,W,C).
+ * smrt_nn_bias_act_bwd_blocked: dz = da * SiLU'(z) (or da), db += column sums of dz (db may be NULL),
+ *   dzb = half(dz) blocked -- the operand of smrt_nn_conv3_wgrad_tma and of the input-gradient
+ *   smrt_nn_conv3_tma, so the float32 dz need not be written at all.
+ * smrt_nn_avgpool2_blocked: 2x2 average pooling of x (N,H,W,C) into y (N,H/2,W/2,C) and/or yb.
+ * smrt_nn_upcat: the decoder input [up2(a) | b]: a (N,H,W,Ca) upsampled (nearest) to 2H x 2W next
+ *   to the skip b (N,2H,2W,Cb), into y (N,2H,2W,Ca+Cb) and/or yb (Ca % 8 == 0, Cb % 8 == 0).
+ * smrt_nn_upcat_bwd: its adjoint: da (N,H,W,Ca) = sum over each 2x2 block of dy[..., :Ca], db =
+ *   dy[..., Ca:] (Ca % 4 == 0, Cb % 4 == 0; da or db may be NULL). */
+SMRT_API int smrt_nn_bias_act_blocked(const float *x, const float *bias, int N, int H, int W, int C, int act,
+                                      float *z, float *a, void *ab, void *stream);
+SMRT_API int smrt_nn_bias_act_bwd_blocked(const float *da, const float *z, int N, int H, int W, int C, int act,
+                                          float *dz, float *db, void *dzb, void *stream);
+SMRT_API int smrt_nn_avgpool2_blocked(const float *x, int N, int H, int W, int C, float *y, void *yb, void *stream);
+SMRT_API int smrt_nn_upcat(const float *a, int N, int H, int W, int Ca, const float *b, int Cb, float *y, void *yb,
+                           void *stream);
+SMRT_API int smrt_nn_upcat_bwd(const float *dy, int N, int H, int W, int Ca, int Cb, float *da, float *db,
+                               void *stream);
+
 /* 2x2 average pooling (H, W even) and its adjoint. */
 SMRT_API int smrt_nn_avgpool2(const float *x, int N, int H, int W, int C, float *y, void *stream);
 SMRT_API int smrt_nn_avgpool2_bwd(const float *dy, int N, int H, int W, int C, float *dx, void *stream);

@@ -72,6 +72,13 @@ SIGNATURES = [
     ("smrt_nn_to_half_rows", c_int, [c_void_p, c_longlong, c_int, ctypes.c_float, c_void_p, c_int, c_void_p]),
     ("smrt_nn_bias_act", c_int, [c_void_p, c_void_p, c_longlong, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     ("smrt_nn_bias_act_bwd", c_int, [c_void_p, c_void_p, c_longlong, c_int, c_int, c_void_p, c_void_p, c_void_p]),
+    ("smrt_nn_bias_act_blocked", c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_int, c_void_p, c_void_p,
+                                         c_void_p, c_void_p]),
+    ("smrt_nn_bias_act_bwd_blocked", c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_int, c_void_p,
+                                             c_void_p, c_void_p, c_void_p]),
+    ("smrt_nn_avgpool2_blocked", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
+    ("smrt_nn_upcat", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    ("smrt_nn_upcat_bwd", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     ("smrt_nn_avgpool2", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p]),
     ("smrt_nn_avgpool2_bwd", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p]),
     ("smrt_nn_upsample2", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p]),

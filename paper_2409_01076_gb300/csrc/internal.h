@@ -2,6 +2,7 @@
 // kernel translation units (prec_*.cu).  Not part of the public interface.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 
@@ -55,6 +56,19 @@ const KernelTable &kernels_f64();
 const KernelTable &kernels_f32();
 const KernelTable &kernels_f16();
 const KernelTable &kernels_bf16();
+
+// Vectorised / fused element-wise kernels of the U-Net (nn_vec.cu).  Each returns
+// cudaErrorNotSupported, launching nothing, when the channel count or alignment rules it out.
+cudaError_t vec_bias_act(const float *x, const float *bias, long long rows, int C, int act, float *z, float *a,
+                         __half *ab, int HW, cudaStream_t s);
+cudaError_t vec_bias_act_bwd(const float *da, const float *z, long long rows, int C, int act, float *dz, float *db,
+                             __half *dzb, int HW, cudaStream_t s);
+cudaError_t vec_avgpool2(const float *x, int N, int H, int W, int C, float *y, __half *yb, cudaStream_t s);
+cudaError_t vec_avgpool2_bwd(const float *dy, int N, int H, int W, int C, float *dx, cudaStream_t s);
+cudaError_t vec_add(const float *a, const float *b, long long n, float *y, cudaStream_t s);
+cudaError_t vec_upcat(const float *a, int N, int H, int W, int Ca, const float *b, int Cb, float *y, __half *yb,
+                      cudaStream_t s);
+cudaError_t vec_upcat_bwd(const float *dy, int N, int H, int W, int Ca, int Cb, float *da, float *db, cudaStream_t s);
 
 // Records the message smrt_last_error(NULL) returns on the calling thread
 // (entry points that take no handle report their errors here).

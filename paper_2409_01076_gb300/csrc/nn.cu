@@ -390,6 +390,12 @@ int nn_fail(int code, const char *fmt, ...)
     return code;
 }
 
+// Status of a launch whose error the launcher already fetched.
+int vec_done(cudaError_t e, const char *what)
+{
+    return e == cudaSuccess ? SMRT_OK : nn_fail(SMRT_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
 int launched(const char *what)
 {
     cudaError_t e = cudaGetLastError();
@@ -477,6 +483,8 @@ int smrt_nn_bias_act(const float *x, const float *bias, long long rows, int C, i
 {
     if (!x || !a || rows < 0 || C < 1) return nn_fail(SMRT_ERR_ARG, "smrt_nn_bias_act: bad arguments");
     if (rows == 0) return SMRT_OK;
+    const cudaError_t e = smrt::vec_bias_act(x, bias, rows, C, act, z, a, nullptr, 1, (cudaStream_t)stream);
+    if (e != cudaErrorNotSupported) return vec_done(e, "smrt_nn_bias_act");
     bias_act_kernel<<<grid_for(rows * C), 256, 0, (cudaStream_t)stream>>>(x, bias, rows, C, act, z, a);
     return launched("smrt_nn_bias_act");
 }
@@ -487,6 +495,8 @@ int smrt_nn_bias_act_bwd(const float *da, const float *z, long long rows, int C,
     if (!da || !dz || (act && !z) || rows < 0 || C < 1 || C > 4096)
         return nn_fail(SMRT_ERR_ARG, "smrt_nn_bias_act_bwd: bad arguments");
     if (rows == 0) return SMRT_OK;
+    const cudaError_t e = smrt::vec_bias_act_bwd(da, z, rows, C, act, dz, db, nullptr, 1, (cudaStream_t)stream);
+    if (e != cudaErrorNotSupported) return vec_done(e, "smrt_nn_bias_act_bwd");
     bias_act_bwd_kernel<<<grid_for(rows * C), 256, C * sizeof(float), (cudaStream_t)stream>>>(da, z, rows, C, act, dz,
                                                                                                 db);
     return launched("smrt_nn_bias_act_bwd");
@@ -505,6 +515,8 @@ int smrt_nn_avgpool2_bwd(const float *dy, int N, int H, int W, int C, float *dx,
 {
     if (!dy || !dx || N < 1 || H < 2 || W < 2 || C < 1 || (H & 1) || (W & 1))
         return nn_fail(SMRT_ERR_ARG, "smrt_nn_avgpool2_bwd: bad arguments");
+    const cudaError_t e = smrt::vec_avgpool2_bwd(dy, N, H, W, C, dx, (cudaStream_t)stream);
+    if (e != cudaErrorNotSupported) return vec_done(e, "smrt_nn_avgpool2_bwd");
     avgpool2_bwd_kernel<<<grid_for((long long)N * H * W * C), 256, 0, (cudaStream_t)stream>>>(dy, N, H, W, C, dx);
     return launched("smrt_nn_avgpool2_bwd");
 }
@@ -544,8 +556,66 @@ int smrt_nn_add(const float *a, const float *b, long long n, float *y, void *str
 {
     if (!a || !b || !y || n < 0) return nn_fail(SMRT_ERR_ARG, "smrt_nn_add: bad arguments");
     if (n == 0) return SMRT_OK;
+    const cudaError_t e = smrt::vec_add(a, b, n, y, (cudaStream_t)stream);
+    if (e != cudaErrorNotSupported) return vec_done(e, "smrt_nn_add");
     add_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(a, b, n, y);
     return launched("smrt_nn_add");
+}
+
+int smrt_nn_bias_act_blocked(const float *x, const float *bias, int N, int H, int W, int C, int act, float *z,
+                             float *a, void *ab, void *stream)
+{
+    if (!x || N < 1 || H < 1 || W < 1 || C < 8 || C % 8 != 0 || (long long)N * H * W * C >= (1LL << 31))
+        return nn_fail(SMRT_ERR_ARG, "smrt_nn_bias_act_blocked: bad arguments (N %d H %d W %d C %d; C %% 8 == 0)", N,
+                       H, W, C);
+    const cudaError_t e = smrt::vec_bias_act(x, bias, (long long)N * H * W, C, act, z, a, (__half *)ab, H * W,
+                                             (cudaStream_t)stream);
+    if (e == cudaErrorNotSupported) return nn_fail(SMRT_ERR_ARG, "smrt_nn_bias_act_blocked: misaligned pointer");
+    return vec_done(e, "smrt_nn_bias_act_blocked");
+}
+
+int smrt_nn_bias_act_bwd_blocked(const float *da, const float *z, int N, int H, int W, int C, int act, float *dz,
+                                 float *db, void *dzb, void *stream)
+{
+    if (!da || (act && !z) || N < 1 || H < 1 || W < 1 || C < 8 || C % 8 != 0 || C > 4096 ||
+        (long long)N * H * W * C >= (1LL << 31))
+        return nn_fail(SMRT_ERR_ARG, "smrt_nn_bias_act_bwd_blocked: bad arguments (N %d H %d W %d C %d; C %% 8 == 0)",
+                       N, H, W, C);
+    const cudaError_t e = smrt::vec_bias_act_bwd(da, z, (long long)N * H * W, C, act, dz, db, (__half *)dzb, H * W,
+                                                 (cudaStream_t)stream);
+    if (e == cudaErrorNotSupported) return nn_fail(SMRT_ERR_ARG, "smrt_nn_bias_act_bwd_blocked: misaligned pointer");
+    return vec_done(e, "smrt_nn_bias_act_bwd_blocked");
+}
+
+int smrt_nn_avgpool2_blocked(const float *x, int N, int H, int W, int C, float *y, void *yb, void *stream)
+{
+    if (!x || N < 1 || H < 2 || W < 2 || (H & 1) || (W & 1) || C < 8 || C % 8 != 0)
+        return nn_fail(SMRT_ERR_ARG, "smrt_nn_avgpool2_blocked: bad arguments (N %d H %d W %d C %d)", N, H, W, C);
+    const cudaError_t e = smrt::vec_avgpool2(x, N, H, W, C, y, (__half *)yb, (cudaStream_t)stream);
+    if (e == cudaErrorNotSupported)
+        return nn_fail(SMRT_ERR_ARG, "smrt_nn_avgpool2_blocked: misaligned pointer or too many elements");
+    return vec_done(e, "smrt_nn_avgpool2_blocked");
+}
+
+int smrt_nn_upcat(const float *a, int N, int H, int W, int Ca, const float *b, int Cb, float *y, void *yb,
+                  void *stream)
+{
+    const uintptr_t al = reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b) |
+                         reinterpret_cast<uintptr_t>(y) | reinterpret_cast<uintptr_t>(yb);
+    if (!a || !b || N < 1 || H < 1 || W < 1 || Ca < 8 || Cb < 8 || Ca % 8 || Cb % 8 || (al & 15) ||
+        4LL * N * H * W * (Ca + Cb) >= (1LL << 31))
+        return nn_fail(SMRT_ERR_ARG, "smrt_nn_upcat: bad arguments (N %d H %d W %d Ca %d Cb %d)", N, H, W, Ca, Cb);
+    return vec_done(smrt::vec_upcat(a, N, H, W, Ca, b, Cb, y, (__half *)yb, (cudaStream_t)stream), "smrt_nn_upcat");
+}
+
+int smrt_nn_upcat_bwd(const float *dy, int N, int H, int W, int Ca, int Cb, float *da, float *db, void *stream)
+{
+    const uintptr_t al = reinterpret_cast<uintptr_t>(dy) | reinterpret_cast<uintptr_t>(da) |
+                         reinterpret_cast<uintptr_t>(db);
+    if (!dy || N < 1 || H < 1 || W < 1 || Ca < 4 || Cb < 4 || Ca % 4 || Cb % 4 || (al & 15) ||
+        4LL * N * H * W * (Ca + Cb) >= (1LL << 31))
+        return nn_fail(SMRT_ERR_ARG, "smrt_nn_upcat_bwd: bad arguments (N %d H %d W %d Ca %d Cb %d)", N, H, W, Ca, Cb);
+    return vec_done(smrt::vec_upcat_bwd(dy, N, H, W, Ca, Cb, da, db, (cudaStream_t)stream), "smrt_nn_upcat_bwd");
 }
 
 int smrt_nn_mse(const float *y, const float *t, long long n, float grad_scale, double *loss, float *dy, void *stream)

@@ -144,6 +144,37 @@ def smrt_nn_add(a, b, y):
     _check(_lib.load().smrt_nn_add(_p(a), _p(b), a.numel(), _p(y), _s()))
 
 
+def smrt_nn_bias_act_blocked(x, bias, act, z, a, ab):
+    """x: (N, H, W, C) float32 (C % 8 == 0); z, a: like x or None; ab: N*C*H*W halves (blocked) or None."""
+    n, h, w, c = x.shape
+    _check(_lib.load().smrt_nn_bias_act_blocked(_p(x), _p(bias), n, h, w, c, int(act), _p(z), _p(a), _p(ab), _s()))
+
+
+def smrt_nn_bias_act_bwd_blocked(da, z, act, dz, db, dzb):
+    """da: (N, H, W, C) float32; dz like da or None; db (C) accumulated or None; dzb blocked halves or None."""
+    n, h, w, c = da.shape
+    _check(_lib.load().smrt_nn_bias_act_bwd_blocked(_p(da), _p(z), n, h, w, c, int(act), _p(dz), _p(db), _p(dzb),
+                                                    _s()))
+
+
+def smrt_nn_avgpool2_blocked(x, y, yb):
+    """x: (N, H, W, C) float32; y: (N, H/2, W/2, C) float32 or None; yb: blocked halves or None."""
+    n, h, w, c = x.shape
+    _check(_lib.load().smrt_nn_avgpool2_blocked(_p(x), n, h, w, c, _p(y), _p(yb), _s()))
+
+
+def smrt_nn_upcat(a, b, y, yb):
+    """a: (N, H, W, Ca); b: (N, 2H, 2W, Cb); y: (N, 2H, 2W, Ca + Cb) float32 or None; yb: blocked or None."""
+    n, h, w, ca = a.shape
+    _check(_lib.load().smrt_nn_upcat(_p(a), n, h, w, ca, _p(b), int(b.shape[3]), _p(y), _p(yb), _s()))
+
+
+def smrt_nn_upcat_bwd(dy, ca, da, db):
+    """dy: (N, 2H, 2W, Ca + Cb); da: (N, H, W, Ca) or None; db: (N, 2H, 2W, Cb) or None."""
+    n, h2, w2, cy = dy.shape
+    _check(_lib.load().smrt_nn_upcat_bwd(_p(dy), n, h2 // 2, w2 // 2, int(ca), int(cy - ca), _p(da), _p(db), _s()))
+
+
 def smrt_nn_mse(y, t, grad_scale, loss, dy):
     _check(_lib.load().smrt_nn_mse(_p(y), _p(t), y.numel(), float(grad_scale), _p(loss), _p(dy), _s()))
 

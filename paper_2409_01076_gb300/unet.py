@@ -50,6 +50,15 @@ def _pad8(n: int) -> int:
     return (n + 7) // 8 * 8
 
 
+class _Act:
+    """An activation (N, H, W, C): its float32 NHWC tensor `f` and/or its blocked half copy `b`
+    ([N][C/8][H][W][8], the operand layout of the TMA convolutions); either may be None."""
+    __slots__ = ("f", "b", "shape")
+
+    def __init__(self, f, b, shape):
+        self.f, self.b, self.shape = f, b, tuple(shape)
+
+
 class UNet:
     def __init__(self, base: int = 32, cin: int = 3, cout: int = 3, seed: int = 0, device: str = "cuda",
                  gemm: str = "tcgen05", conv: str = "tma"):
@@ -125,37 +134,45 @@ class UNet:
                     self._wfp[name] = t.empty(K.smrt_nn_pack3_halves(ci, co), dtype=t.float16, device=self.device)
                     K.smrt_nn_pack3(f, co, self._wfp[name])
 
-    def _conv(self, spec, x, cache):
+    def _conv(self, spec, inp, cache, out_f=True, out_b=False):
+        """One convolution + bias + activation.  inp: _Act; returns an _Act with the float32 output
+        (out_f) and/or its blocked half copy (out_b, for a TMA convolution that reads it next)."""
         t = self.torch
         name, ci, co, k, act = spec
-        n, h, w, _ = x.shape
+        n, h, w, _ = inp.shape
         rows = n * h * w
         kk = k * k * ci
         y = t.empty((n, h, w, co), dtype=t.float32, device=self.device)
-        xb = None
+        xb = col = None
         if self._tma(k, ci):
             # operands by TMA: blocked half activations, nine taps as shifted views of one haloed tile
-            xb = t.empty(n * h * w * ci, dtype=t.float16, device=self.device)
-            K.smrt_nn_to_half_blocked(x, xb)
-            K.smrt_nn_conv3_tma(xb, (n, h, w, ci), self._wp[name], y, co, 1.0, 0.0, self._gemm_err)
-            col = None
+            xb = inp.b
+            if xb is None:
+                xb = t.empty(rows * ci, dtype=t.float16, device=self.device)
+                K.smrt_nn_to_half_blocked(inp.f, xb)
+            K.smrt_nn_conv3_tma(xb, inp.shape, self._wp[name], y, co, 1.0, 0.0, self._gemm_err)
         elif self._implicit(k, ci):
             # implicit GEMM: the A tiles are gathered from x, no im2col matrix is built
-            K.smrt_nn_conv3_tc(x, self._wh[name], y, 1.0, 0.0, self._gemm_err)
-            col = None
+            K.smrt_nn_conv3_tc(inp.f, self._wh[name], y, 1.0, 0.0, self._gemm_err)
         else:
             ldk = _pad8(kk)             # whole 16-byte rows for the GEMM's vector loads
             col = t.empty((rows, ldk), dtype=t.float16, device=self.device)
             if k == 3:
-                K.smrt_nn_im2col3(x, col)
+                K.smrt_nn_im2col3(inp.f, col)
             else:
-                K.smrt_nn_to_half_rows(x.view(rows, ci), col)
+                K.smrt_nn_to_half_rows(inp.f.view(rows, ci), col)
             self._gemm(0, 1, rows, co, kk, 1.0, col, ldk, self._wh[name], kk, 0.0, y, co)
         z = t.empty_like(y) if (act and cache is not None) else None
-        K.smrt_nn_bias_act(y, self.params[name + ".b"], act, z, y)
+        ab = None
+        if out_b and self._blocked_ok(co):
+            ab = t.empty(rows * co, dtype=t.float16, device=self.device)
+            K.smrt_nn_bias_act_blocked(y, self.params[name + ".b"], act, z, y if out_f else None, ab)
+        else:
+            out_f = True
+            K.smrt_nn_bias_act(y, self.params[name + ".b"], act, z, y)
         if cache is not None:
-            cache[name] = (col, z, x, xb)
-        return y
+            cache[name] = (col, z, inp.f, xb, inp.shape)
+        return _Act(y if out_f else None, ab, (n, h, w, co))
 
     def _implicit(self, k, c):
         """3x3 convolutions over C % 8 == 0 channels run as implicit GEMMs on the tcgen05 backend."""
@@ -165,41 +182,45 @@ class UNet:
         """... and with TMA-fed operands when C % 16 == 0, unless the gather path was chosen."""
         return self.conv_path == "tma" and self._implicit(k, c) and c % 16 == 0
 
+    def _blocked_ok(self, c):
+        """Whether a c-channel activation may be handed over as blocked halves only."""
+        return self.conv_path == "tma" and self.gemm_backend == "tcgen05" and c % 8 == 0
+
+    def _reads_blocked(self, spec):
+        """A convolution whose forward and weight gradient read only the blocked half input."""
+        _, ci, co, k, _ = spec
+        return self._tma(k, ci) and co % 8 == 0
+
     def _conv_bwd(self, spec, da, cache, need_dx=True):
         t = self.torch
         name, ci, co, k, act = spec
-        col, z, x, xb = cache[name]
-        xshape = x.shape
+        col, z, xf, xb, xshape = cache[name]
         n, h, w, _ = xshape
         rows = n * h * w
         kk = k * k * ci
         ldz = _pad8(co)
-        dz = t.empty_like(da)
-        K.smrt_nn_bias_act_bwd(da, z, act, dz, self.grads[name + ".b"])
         gw = self.grads[name + ".w"]
-        dzb = dzh = None
-
-        def blocked_dz():
-            d = t.empty(rows * co, dtype=t.float16, device=self.device)
-            K.smrt_nn_to_half_blocked(dz, d)
-            return d
-
-        def half_dz():
-            d = t.empty((rows, ldz), dtype=t.float16, device=self.device)
-            K.smrt_nn_to_half_rows(dz.view(rows, co), d)
-            return d
-
-        if xb is not None and co % 8 == 0:
-            # TMA weight gradient from the blocked halves of x (kept by the forward) and of dz
-            dzb = blocked_dz()
-            K.smrt_nn_conv3_wgrad_tma(xb, (n, h, w, ci), dzb, co, gw, 1.0, self._gemm_err)
+        tma_w = xb is not None and co % 8 == 0              # weight gradient from blocked halves
+        tma_dx = need_dx and k == 3 and self._tma(k, co)    # input gradient by the TMA convolution
+        dzf = t.empty_like(da) if (not tma_w or (need_dx and not tma_dx)) else None
+        dzb = None
+        if tma_w or tma_dx:
+            dzb = t.empty(rows * co, dtype=t.float16, device=self.device)
+            K.smrt_nn_bias_act_bwd_blocked(da, z, act, dzf, self.grads[name + ".b"], dzb)
+        else:
+            K.smrt_nn_bias_act_bwd(da, z, act, dzf, self.grads[name + ".b"])
+        dzh = None
+        if tma_w:
+            K.smrt_nn_conv3_wgrad_tma(xb, xshape, dzb, co, gw, 1.0, self._gemm_err)
         else:
             if col is None:         # the forward gathered from x; the weight gradient needs the matrix
                 col = t.empty((rows, _pad8(kk)), dtype=t.float16, device=self.device)
-                K.smrt_nn_im2col3(x, col)
+                K.smrt_nn_im2col3(xf, col)
             ldk = col.shape[1]
-            dzh = half_dz()
-            split = max(1, min(256, rows // 8192))
+            dzh = t.empty((rows, ldz), dtype=t.float16, device=self.device)
+            K.smrt_nn_to_half_rows(dzf.view(rows, co), dzh)
+            # many split-K blocks: K is the pixel count, M and N are small
+            split = max(1, min(1024, rows // 1024))
             if self.gemm_backend == "tcgen05":
                 # dW^T = col^T dz: the 9 cin dimension on the tensor core's M = 128 side, stored transposed
                 K.smrt_nn_gemm_tc(1, 2, kk, co, rows, 1.0, col, ldk, dzh, ldz, 1.0, gw, kk, split, self._gemm_err)
@@ -209,54 +230,78 @@ class UNet:
             return None
         dx = t.empty(xshape, dtype=t.float32, device=self.device)
         if k == 1:
-            dzh = half_dz() if dzh is None else dzh
             self._gemm(0, 0, rows, ci, co, 1.0, dzh, ldz, self._wh[name], ci, 0.0, dx, ci)
             return dx
         # dx = conv3(dz, flip(W)): the adjoint 3x3 convolution, no col2im
-        if self._tma(k, co):
-            dzb = blocked_dz() if dzb is None else dzb
+        if tma_dx:
             K.smrt_nn_conv3_tma(dzb, (n, h, w, co), self._wfp[name], dx, ci, 1.0, 0.0, self._gemm_err)
             return dx
         if self._implicit(k, co):
-            K.smrt_nn_conv3_tc(dz.view(n, h, w, co), self._wf[name], dx, 1.0, 0.0, self._gemm_err)
+            K.smrt_nn_conv3_tc(dzf.view(n, h, w, co), self._wf[name], dx, 1.0, 0.0, self._gemm_err)
             return dx
         dzcol = t.empty((rows, 9 * co), dtype=t.float16, device=self.device)
-        K.smrt_nn_im2col3(dz.view(n, h, w, co), dzcol)
+        K.smrt_nn_im2col3(dzf.view(n, h, w, co), dzcol)
         self._gemm(0, 1, rows, ci, 9 * co, 1.0, dzcol, 9 * co, self._wf[name], 9 * co, 0.0, dx, ci)
         return dx
 
     # ---- the network ------------------------------------------------------------------
-    def _pool(self, x):
+    def _pool(self, x, blocked):
+        """2x2 average pooling of x (_Act with float32); blocked: hand over the blocked halves only."""
+        t = self.torch
         n, h, w, c = x.shape
-        y = self.torch.empty((n, h // 2, w // 2, c), dtype=self.torch.float32, device=self.device)
-        K.smrt_nn_avgpool2(x, y)
-        return y
+        shape = (n, h // 2, w // 2, c)
+        if blocked and self._blocked_ok(c):
+            yb = t.empty(n * (h // 2) * (w // 2) * c, dtype=t.float16, device=self.device)
+            K.smrt_nn_avgpool2_blocked(x.f, None, yb)
+            return _Act(None, yb, shape)
+        y = t.empty(shape, dtype=t.float32, device=self.device)
+        if c % 8 == 0:
+            K.smrt_nn_avgpool2_blocked(x.f, y, None)        # the vectorised kernel, float32 output only
+        else:
+            K.smrt_nn_avgpool2(x.f, y)
+        return _Act(y, None, shape)
 
-    def _up(self, x):
-        n, h, w, c = x.shape
-        y = self.torch.empty((n, 2 * h, 2 * w, c), dtype=self.torch.float32, device=self.device)
-        K.smrt_nn_upsample2(x, y)
-        return y
-
-    def _cat(self, a, b):
+    def _upcat(self, a, b, blocked):
+        """The decoder input [up2(a) | b] (a, b: _Act with float32)."""
+        t = self.torch
         n, h, w, ca = a.shape
-        y = self.torch.empty((n, h, w, ca + b.shape[3]), dtype=self.torch.float32, device=self.device)
-        K.smrt_nn_concat(a, b, y)
-        return y
+        cb = b.shape[3]
+        shape = (n, 2 * h, 2 * w, ca + cb)
+        if ca % 8 == 0 and cb % 8 == 0:
+            yb = None
+            if blocked and self._blocked_ok(ca + cb):
+                yb = t.empty(n * 4 * h * w * (ca + cb), dtype=t.float16, device=self.device)
+                K.smrt_nn_upcat(a.f, b.f, None, yb)
+                return _Act(None, yb, shape)
+            y = t.empty(shape, dtype=t.float32, device=self.device)
+            K.smrt_nn_upcat(a.f, b.f, y, None)
+            return _Act(y, None, shape)
+        u = t.empty((n, 2 * h, 2 * w, ca), dtype=t.float32, device=self.device)
+        K.smrt_nn_upsample2(a.f, u)
+        y = t.empty(shape, dtype=t.float32, device=self.device)
+        K.smrt_nn_concat(u, b.f, y)
+        return _Act(y, None, shape)
 
     def forward(self, x, cache=None):
-        """x: (N, H, W, cin) float32 CUDA, H and W divisible by 8.  Returns (N, H, W, cout)."""
+        """x: (N, H, W, cin) float32 CUDA, H and W divisible by 8.  Returns (N, H, W, cout).
+        Where the next convolution reads TMA tiles, an activation is handed over as blocked halves
+        only (no float32 copy is written)."""
         s = {sp[0]: sp for sp in self.specs}
         self._half_weights()
-        c = lambda name, inp: self._conv(s[name], inp, cache)  # noqa: E731
-        e1 = c("enc1b", c("enc1a", x))
-        e2 = c("enc2b", c("enc2a", self._pool(e1)))
-        e3 = c("enc3b", c("enc3a", self._pool(e2)))
-        m = c("midb", c("mida", self._pool(e3)))
-        d3 = c("dec3b", c("dec3a", self._cat(self._up(m), e3)))
-        d2 = c("dec2b", c("dec2a", self._cat(self._up(d3), e2)))
-        d1 = c("dec1b", c("dec1a", self._cat(self._up(d2), e1)))
-        return c("head", d1)
+        rb = lambda name: self._reads_blocked(s[name])  # noqa: E731
+
+        def c(name, inp, nxt=None):     # nxt: the convolution that reads the output, if only one does
+            b = nxt is not None and rb(nxt)
+            return self._conv(s[name], inp, cache, out_f=not b, out_b=b)
+
+        e1 = c("enc1b", c("enc1a", _Act(x, None, tuple(x.shape)), "enc1b"))
+        e2 = c("enc2b", c("enc2a", self._pool(e1, rb("enc2a")), "enc2b"))
+        e3 = c("enc3b", c("enc3a", self._pool(e2, rb("enc3a")), "enc3b"))
+        m = c("midb", c("mida", self._pool(e3, rb("mida")), "midb"))
+        d3 = c("dec3b", c("dec3a", self._upcat(m, e3, rb("dec3a")), "dec3b"))
+        d2 = c("dec2b", c("dec2a", self._upcat(d3, e2, rb("dec2a")), "dec2b"))
+        d1 = c("dec1b", c("dec1a", self._upcat(d2, e1, rb("dec1a")), "dec1b"))
+        return c("head", d1).f
 
     def backward(self, dy, cache):
         """Accumulates scaled gradients of the loss into self.grads from dL/dy (already scaled)."""
@@ -265,18 +310,18 @@ class UNet:
         b = self.base
         cb = lambda name, da, need=True: self._conv_bwd(s[name], da, cache, need)  # noqa: E731
 
-        def split(dcat, ca):
-            n, h, w, cc = dcat.shape
-            da = t.empty((n, h, w, ca), dtype=t.float32, device=self.device)
-            db = t.empty((n, h, w, cc - ca), dtype=t.float32, device=self.device)
-            K.smrt_nn_concat_bwd(dcat, ca, cc - ca, da, db)
+        def upcat_bwd(dcat, ca):
+            """Gradients of the low-resolution input and of the skip from that of [up2(a) | skip]."""
+            n, h2, w2, cc = dcat.shape
+            da = t.empty((n, h2 // 2, w2 // 2, ca), dtype=t.float32, device=self.device)
+            db = t.empty((n, h2, w2, cc - ca), dtype=t.float32, device=self.device)
+            if ca % 4 == 0 and (cc - ca) % 4 == 0:
+                K.smrt_nn_upcat_bwd(dcat, ca, da, db)
+                return da, db
+            du = t.empty((n, h2, w2, ca), dtype=t.float32, device=self.device)
+            K.smrt_nn_concat_bwd(dcat, ca, cc - ca, du, db)
+            K.smrt_nn_upsample2_bwd(du, (n, h2 // 2, w2 // 2, ca), da)
             return da, db
-
-        def up_bwd(dyy):
-            n, h, w, cc = dyy.shape
-            dx = t.empty((n, h // 2, w // 2, cc), dtype=t.float32, device=self.device)
-            K.smrt_nn_upsample2_bwd(dyy, (n, h // 2, w // 2, cc), dx)
-            return dx
 
         def pool_bwd(dyy):
             n, h, w, cc = dyy.shape
@@ -289,10 +334,10 @@ class UNet:
             return acc
 
         dd1 = cb("head", dy)
-        du2, de1 = split(cb("dec1a", cb("dec1b", dd1)), 2 * b)
-        du3, de2 = split(cb("dec2a", cb("dec2b", up_bwd(du2))), 4 * b)
-        dum, de3 = split(cb("dec3a", cb("dec3b", up_bwd(du3))), 8 * b)
-        de3 = add_into(de3, pool_bwd(cb("mida", cb("midb", up_bwd(dum)))))
+        du2, de1 = upcat_bwd(cb("dec1a", cb("dec1b", dd1)), 2 * b)
+        du3, de2 = upcat_bwd(cb("dec2a", cb("dec2b", du2)), 4 * b)
+        dum, de3 = upcat_bwd(cb("dec3a", cb("dec3b", du3)), 8 * b)
+        de3 = add_into(de3, pool_bwd(cb("mida", cb("midb", dum))))
         de2 = add_into(de2, pool_bwd(cb("enc3a", cb("enc3b", de3))))
         de1 = add_into(de1, pool_bwd(cb("enc2a", cb("enc2b", de2))))
         cb("enc1a", cb("enc1b", de1), need=False)

@@ -134,6 +134,79 @@ def test_pool_upsample_concat_add():
     assert np.abs(_np(s) - 2 * x).max() < 1e-5
 
 
+@pytest.mark.parametrize("C", [12, 16])
+def test_vector_elementwise_paths(C):
+    """The 16-byte-vector kernels behind the plain entry points (C % 4 == 0) and the fused forms that
+    write the blocked half layout, against numpy."""
+    import torch
+    r = _rng(40 + C)
+    n, h, w = 2, 6, 10
+    x = r.normal(size=(n, h, w, C)) * 3
+    b = r.normal(size=(C,))
+    z = torch.empty((n, h, w, C), device="cuda")
+    a = torch.empty((n, h, w, C), device="cuda")
+    S.smrt_nn_bias_act(_t(x), _t(b), 1, z, a)
+    zr = x + b
+    assert np.abs(_np(z) - zr).max() < 1e-5 and np.abs(_np(a) - U.silu(zr)).max() < 1e-5
+    da = r.normal(size=(n, h, w, C))
+    dz = torch.empty((n, h, w, C), device="cuda")
+    db = torch.zeros(C, device="cuda")
+    S.smrt_nn_bias_act_bwd(_t(da), z, 1, dz, db)
+    dzr = da * U.silu_grad(zr)
+    assert np.abs(_np(dz) - dzr).max() < 1e-5
+    assert np.abs(_np(db) - dzr.reshape(-1, C).sum(axis=0)).max() < 1e-4
+    y = torch.empty((n, h // 2, w // 2, C), device="cuda")
+    S.smrt_nn_avgpool2(_t(x), y)
+    dx = torch.empty((n, h, w, C), device="cuda")
+    S.smrt_nn_avgpool2_bwd(y, (n, h, w, C), dx)
+    assert np.abs(_np(dx) - U.pool_bwd(U.pool(x))).max() < 1e-5
+    s2 = torch.empty((n, h, w, C), device="cuda")
+    S.smrt_nn_add(_t(x), _t(da), s2)
+    assert np.abs(_np(s2) - (x + da)).max() < 1e-5
+    if C % 8:
+        return
+
+    def blocked(v):
+        return v.reshape(n, v.shape[1], v.shape[2], C // 8, 8).transpose(0, 3, 1, 2, 4).ravel()
+
+    ab = torch.empty(x.size, dtype=torch.float16, device="cuda")
+    z2 = torch.empty((n, h, w, C), device="cuda")
+    S.smrt_nn_bias_act_blocked(_t(x), _t(b), 1, z2, None, ab)
+    assert np.array_equal(_np(z2), _np(z))
+    assert np.array_equal(ab.cpu().numpy(), blocked(_np(a).astype(np.float32)).astype(np.float16))
+    dzb = torch.empty(x.size, dtype=torch.float16, device="cuda")
+    db2 = torch.zeros(C, device="cuda")
+    S.smrt_nn_bias_act_bwd_blocked(_t(da), z, 1, None, db2, dzb)
+    assert np.array_equal(dzb.cpu().numpy(), blocked(_np(dz).astype(np.float32)).astype(np.float16))
+    assert np.abs(_np(db2) - _np(db)).max() < 1e-5
+    yb = torch.empty(y.numel(), dtype=torch.float16, device="cuda")
+    y2 = torch.empty_like(y)
+    S.smrt_nn_avgpool2_blocked(_t(x), y2, yb)
+    assert np.abs(_np(y2) - U.pool(x)).max() < 1e-6
+    assert np.array_equal(yb.cpu().numpy(), blocked(_np(y2).astype(np.float32)).astype(np.float16))
+
+
+def test_upcat_and_its_adjoint():
+    import torch
+    r = _rng(41)
+    n, h, w, ca, cb = 2, 3, 5, 16, 8
+    a = r.normal(size=(n, h, w, ca))
+    b = r.normal(size=(n, 2 * h, 2 * w, cb))
+    ref = np.concatenate([U.up(a), b], axis=3)
+    y = torch.empty(ref.shape, device="cuda")
+    yb = torch.empty(ref.size, dtype=torch.float16, device="cuda")
+    S.smrt_nn_upcat(_t(a), _t(b), y, yb)
+    assert np.array_equal(_np(y), ref.astype(np.float32).astype(np.float64))
+    blk = ref.reshape(n, 2 * h, 2 * w, (ca + cb) // 8, 8).transpose(0, 3, 1, 2, 4).ravel()
+    assert np.array_equal(yb.cpu().numpy(), blk.astype(np.float32).astype(np.float16))
+    dy = r.normal(size=ref.shape)
+    da = torch.empty((n, h, w, ca), device="cuda")
+    db = torch.empty((n, 2 * h, 2 * w, cb), device="cuda")
+    S.smrt_nn_upcat_bwd(_t(dy), ca, da, db)
+    assert np.abs(_np(da) - U.up_bwd(dy[..., :ca])).max() < 1e-5
+    assert np.array_equal(_np(db), dy[..., ca:].astype(np.float32).astype(np.float64))
+
+
 def test_mse_and_adam():
     import torch
     r = _rng(6)
