@@ -162,6 +162,16 @@ SMRT_API int smrt_nn_upcat(const float *a, int N, int H, int W, int Ca, const fl
 SMRT_API int smrt_nn_upcat_bwd(const float *dy, int N, int H, int W, int Ca, int Cb, float *da, float *db,
                                void *stream);
 
+/* 1x1 convolution with at most 3 outputs (the network's head), float32 on the CUDA cores:
+ *   y[p][o] = sum_c x[p][c] w[o][c] + bias[o]      (P pixels, x: P x C, w: cout x C, y: P x cout)
+ * and its backward dx[p][c] = sum_o dy[p][o] w[o][c], dw[o][c] += sum_p dy[p][o] x[p][c],
+ * db[o] += sum_p dy[p][o] (dx, dw, db may each be NULL; dw, db accumulate with atomics).
+ * 4 <= C <= 64, C % 4 == 0, x (and dx) 16-byte aligned; bias may be NULL. */
+SMRT_API int smrt_nn_conv1x1_small(const float *x, long long P, int C, const float *w, const float *bias, int cout,
+                                   float *y, void *stream);
+SMRT_API int smrt_nn_conv1x1_small_bwd(const float *dy, const float *x, long long P, int C, const float *w, int cout,
+                                       float *dx, float *dw, float *db, void *stream);
+
 /* 2x2 average pooling (H, W even) and its adjoint. */
 SMRT_API int smrt_nn_avgpool2(const float *x, int N, int H, int W, int C, float *y, void *stream);
 SMRT_API int smrt_nn_avgpool2_bwd(const float *dy, int N, int H, int W, int C, float *dx, void *stream);

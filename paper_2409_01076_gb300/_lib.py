@@ -79,6 +79,9 @@ SIGNATURES = [
     ("smrt_nn_avgpool2_blocked", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     ("smrt_nn_upcat", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     ("smrt_nn_upcat_bwd", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
+    ("smrt_nn_conv1x1_small", c_int, [c_void_p, c_longlong, c_int, c_void_p, c_void_p, c_int, c_void_p, c_void_p]),
+    ("smrt_nn_conv1x1_small_bwd", c_int, [c_void_p, c_void_p, c_longlong, c_int, c_void_p, c_int, c_void_p, c_void_p,
+                                          c_void_p, c_void_p]),
     ("smrt_nn_avgpool2", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p]),
     ("smrt_nn_avgpool2_bwd", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p]),
     ("smrt_nn_upsample2", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p]),

@@ -70,6 +70,11 @@ cudaError_t vec_upcat(const float *a, int N, int H, int W, int Ca, const float *
                       cudaStream_t s);
 cudaError_t vec_upcat_bwd(const float *dy, int N, int H, int W, int Ca, int Cb, float *da, float *db, cudaStream_t s);
 
+cudaError_t small_conv1x1(const float *x, long long P, int C, const float *w, const float *bias, int cout, float *y,
+                          cudaStream_t s);
+cudaError_t small_conv1x1_bwd(const float *dy, const float *x, long long P, int C, const float *w, int cout, float *dx,
+                              float *dw, float *db, cudaStream_t s);
+
 // Records the message smrt_last_error(NULL) returns on the calling thread
 // (entry points that take no handle report their errors here).
 void set_thread_error(const char *msg);

@@ -618,6 +618,25 @@ int smrt_nn_upcat_bwd(const float *dy, int N, int H, int W, int Ca, int Cb, floa
     return vec_done(smrt::vec_upcat_bwd(dy, N, H, W, Ca, Cb, da, db, (cudaStream_t)stream), "smrt_nn_upcat_bwd");
 }
 
+int smrt_nn_conv1x1_small(const float *x, long long P, int C, const float *w, const float *bias, int cout, float *y,
+                          void *stream)
+{
+    if (!x || !w || !y || P < 1 || P >= (1LL << 31) || C < 4 || C > 64 || C % 4 || cout < 1 || cout > 3 ||
+        (reinterpret_cast<uintptr_t>(x) & 15))
+        return nn_fail(SMRT_ERR_ARG, "smrt_nn_conv1x1_small: bad arguments (P %lld C %d cout %d)", P, C, cout);
+    return vec_done(smrt::small_conv1x1(x, P, C, w, bias, cout, y, (cudaStream_t)stream), "smrt_nn_conv1x1_small");
+}
+
+int smrt_nn_conv1x1_small_bwd(const float *dy, const float *x, long long P, int C, const float *w, int cout, float *dx,
+                              float *dw, float *db, void *stream)
+{
+    if (!dy || !x || !w || P < 1 || P >= (1LL << 31) || C < 4 || C > 64 || C % 4 || cout < 1 || cout > 3 ||
+        ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(dx)) & 15))
+        return nn_fail(SMRT_ERR_ARG, "smrt_nn_conv1x1_small_bwd: bad arguments (P %lld C %d cout %d)", P, C, cout);
+    return vec_done(smrt::small_conv1x1_bwd(dy, x, P, C, w, cout, dx, dw, db, (cudaStream_t)stream),
+                    "smrt_nn_conv1x1_small_bwd");
+}
+
 int smrt_nn_mse(const float *y, const float *t, long long n, float grad_scale, double *loss, float *dy, void *stream)
 {
     if (!y || !t || !loss || n < 1) return nn_fail(SMRT_ERR_ARG, "smrt_nn_mse: bad arguments");

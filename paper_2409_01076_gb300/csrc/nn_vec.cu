@@ -215,6 +215,100 @@ __global__ void add_vec(const float *a, const float *b, int n4, float *y)
     }
 }
 
+// 1x1 convolution with few outputs (the network's head), float32 on the CUDA cores: a product of
+// COUT x C per pixel is far too narrow for the tensor cores and is bound by reading x.
+// Forward: y[p][o] = sum_c x[p][c] w[o][c] + b[o].  Thread: one pixel.
+template <int COUT>
+__global__ void conv1x1_small(const float *__restrict__ x, int P, int C, const float *__restrict__ w,
+                              const float *__restrict__ bias, float *__restrict__ y)
+{
+    extern __shared__ float sw[];           // COUT x C weights
+    for (int i = threadIdx.x; i < COUT * C; i += blockDim.x) sw[i] = w[i];
+    __syncthreads();
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+        float acc[COUT];
+        #pragma unroll
+        for (int o = 0; o < COUT; ++o) acc[o] = bias ? bias[o] : 0.0f;
+        const float *xp = x + (size_t)p * C;
+        for (int c = 0; c < C; c += 4) {
+            const Vec<4> v = ldv<4>(xp + c);
+            #pragma unroll
+            for (int o = 0; o < COUT; ++o)
+                #pragma unroll
+                for (int i = 0; i < 4; ++i) acc[o] = fmaf(v.v[i], sw[o * C + c + i], acc[o]);
+        }
+        #pragma unroll
+        for (int o = 0; o < COUT; ++o) y[(size_t)p * COUT + o] = acc[o];
+    }
+}
+
+// Backward of conv1x1_small: dx[p][c] = sum_o dy[p][o] w[o][c]; dw[o][c] += sum_p dy[p][o] x[p][c];
+// db[o] += sum_p dy[p][o].  Thread: one pixel at a time, its share of dw / db in registers; a block
+// adds them up in shared memory and then into dw / db with one atomic per entry.  C <= 64.
+template <int COUT>
+__global__ void __launch_bounds__(128)
+conv1x1_small_bwd(const float *__restrict__ dy, const float *__restrict__ x, int P, int C,
+                  const float *__restrict__ w, float *__restrict__ dx, float *dw, float *db)
+{
+    __shared__ float sw[COUT * 64];
+    __shared__ float sacc[COUT * 64 + COUT];
+    for (int i = threadIdx.x; i < COUT * C; i += blockDim.x) sw[i] = w[i];
+    for (int i = threadIdx.x; i < COUT * C + COUT; i += blockDim.x) sacc[i] = 0.0f;
+    __syncthreads();
+    float gw[COUT][64 / 4][4];
+    float gb[COUT];
+    #pragma unroll
+    for (int o = 0; o < COUT; ++o) {
+        gb[o] = 0.0f;
+        #pragma unroll
+        for (int q = 0; q < 16; ++q)
+            #pragma unroll
+            for (int i = 0; i < 4; ++i) gw[o][q][i] = 0.0f;
+    }
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+        float g[COUT];
+        #pragma unroll
+        for (int o = 0; o < COUT; ++o) {
+            g[o] = dy[(size_t)p * COUT + o];
+            gb[o] += g[o];
+        }
+        const float *xp = x + (size_t)p * C;
+        float *dxp = dx ? dx + (size_t)p * C : nullptr;
+        #pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            if (4 * q >= C) break;
+            const Vec<4> v = ldv<4>(xp + 4 * q);
+            Vec<4> d;
+            #pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float s = 0.0f;
+                #pragma unroll
+                for (int o = 0; o < COUT; ++o) {
+                    gw[o][q][i] = fmaf(g[o], v.v[i], gw[o][q][i]);
+                    s = fmaf(g[o], sw[o * C + 4 * q + i], s);
+                }
+                d.v[i] = s;
+            }
+            if (dxp) stv<4>(dxp + 4 * q, d);
+        }
+    }
+    #pragma unroll
+    for (int o = 0; o < COUT; ++o) {
+        atomicAdd(&sacc[COUT * C + o], gb[o]);
+        #pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            if (4 * q >= C) break;
+            #pragma unroll
+            for (int i = 0; i < 4; ++i) atomicAdd(&sacc[o * C + 4 * q + i], gw[o][q][i]);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < COUT * C; i += blockDim.x)
+        if (dw) atomicAdd(&dw[i], sacc[i]);
+    for (int o = threadIdx.x; o < COUT; o += blockDim.x)
+        if (db) atomicAdd(&db[o], sacc[COUT * C + o]);
+}
+
 bool al16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
 unsigned blocks_for(long long n)
@@ -303,6 +397,33 @@ cudaError_t vec_upcat_bwd(const float *dy, int N, int H, int W, int Ca, int Cb, 
     const long long n = (da ? (long long)N * H * W * (Ca / 4) : 0) + (db ? (long long)N * 4 * H * W * (Cb / 4) : 0);
     if (n == 0) return cudaSuccess;
     upcat_bwd_vec<<<blocks_for(n), 256, 0, s>>>(dy, N, H, W, Ca, Cb, da, db);
+    return cudaGetLastError();
+}
+
+cudaError_t small_conv1x1(const float *x, long long P, int C, const float *w, const float *bias, int cout, float *y,
+                          cudaStream_t s)
+{
+    const unsigned blocks = blocks_for(P);
+    const size_t sm = (size_t)cout * C * sizeof(float);
+    switch (cout) {
+    case 1: conv1x1_small<1><<<blocks, 256, sm, s>>>(x, (int)P, C, w, bias, y); break;
+    case 2: conv1x1_small<2><<<blocks, 256, sm, s>>>(x, (int)P, C, w, bias, y); break;
+    default: conv1x1_small<3><<<blocks, 256, sm, s>>>(x, (int)P, C, w, bias, y); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t small_conv1x1_bwd(const float *dy, const float *x, long long P, int C, const float *w, int cout, float *dx,
+                              float *dw, float *db, cudaStream_t s)
+{
+    long long b = (P + 127) / 128;
+    if (b > 152LL * 4) b = 152LL * 4;
+    const unsigned blocks = (unsigned)(b < 1 ? 1 : b);
+    switch (cout) {
+    case 1: conv1x1_small_bwd<1><<<blocks, 128, 0, s>>>(dy, x, (int)P, C, w, dx, dw, db); break;
+    case 2: conv1x1_small_bwd<2><<<blocks, 128, 0, s>>>(dy, x, (int)P, C, w, dx, dw, db); break;
+    default: conv1x1_small_bwd<3><<<blocks, 128, 0, s>>>(dy, x, (int)P, C, w, dx, dw, db); break;
+    }
     return cudaGetLastError();
 }
 

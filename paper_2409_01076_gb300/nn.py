@@ -144,6 +144,20 @@ def smrt_nn_add(a, b, y):
     _check(_lib.load().smrt_nn_add(_p(a), _p(b), a.numel(), _p(y), _s()))
 
 
+def smrt_nn_conv1x1_small(x, w, bias, y):
+    """x: (..., C) float32; w: (cout, C) float32, cout <= 3; bias: (cout) or None; y: (..., cout)."""
+    c = x.shape[-1]
+    _check(_lib.load().smrt_nn_conv1x1_small(_p(x), x.numel() // c, int(c), _p(w), _p(bias), int(w.shape[0]), _p(y),
+                                             _s()))
+
+
+def smrt_nn_conv1x1_small_bwd(dy, x, w, dx, dw, db):
+    """Backward of smrt_nn_conv1x1_small: dx (like x) written, dw (cout, C) and db (cout) accumulated."""
+    c = x.shape[-1]
+    _check(_lib.load().smrt_nn_conv1x1_small_bwd(_p(dy), _p(x), x.numel() // c, int(c), _p(w), int(w.shape[0]),
+                                                 _p(dx), _p(dw), _p(db), _s()))
+
+
 def smrt_nn_bias_act_blocked(x, bias, act, z, a, ab):
     """x: (N, H, W, C) float32 (C % 8 == 0); z, a: like x or None; ab: N*C*H*W halves (blocked) or None."""
     n, h, w, c = x.shape

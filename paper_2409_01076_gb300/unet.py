@@ -144,6 +144,12 @@ class UNet:
         kk = k * k * ci
         y = t.empty((n, h, w, co), dtype=t.float32, device=self.device)
         xb = col = None
+        if self._small_1x1(spec):
+            # the head: a few float32 dot products per pixel, bias included
+            K.smrt_nn_conv1x1_small(inp.f, self.params[name + ".w"], self.params[name + ".b"], y)
+            if cache is not None:
+                cache[name] = (None, None, inp.f, None, inp.shape)
+            return _Act(y, None, (n, h, w, co))
         if self._tma(k, ci):
             # operands by TMA: blocked half activations, nine taps as shifted views of one haloed tile
             xb = inp.b
@@ -182,6 +188,12 @@ class UNet:
         """... and with TMA-fed operands when C % 16 == 0, unless the gather path was chosen."""
         return self.conv_path == "tma" and self._implicit(k, c) and c % 16 == 0
 
+    @staticmethod
+    def _small_1x1(spec):
+        """A 1x1 convolution without activation and at most 3 outputs: CUDA-core float32 kernels."""
+        _, ci, co, k, act = spec
+        return k == 1 and not act and co <= 3 and ci % 4 == 0 and ci <= 64
+
     def _blocked_ok(self, c):
         """Whether a c-channel activation may be handed over as blocked halves only."""
         return self.conv_path == "tma" and self.gemm_backend == "tcgen05" and c % 8 == 0
@@ -197,6 +209,11 @@ class UNet:
         col, z, xf, xb, xshape = cache[name]
         n, h, w, _ = xshape
         rows = n * h * w
+        if self._small_1x1(spec):
+            dx = t.empty(xshape, dtype=t.float32, device=self.device) if need_dx else None
+            K.smrt_nn_conv1x1_small_bwd(da, xf, self.params[name + ".w"], dx, self.grads[name + ".w"],
+                                        self.grads[name + ".b"])
+            return dx
         kk = k * k * ci
         ldz = _pad8(co)
         gw = self.grads[name + ".w"]

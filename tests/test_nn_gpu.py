@@ -186,6 +186,26 @@ def test_vector_elementwise_paths(C):
     assert np.array_equal(yb.cpu().numpy(), blocked(_np(y2).astype(np.float32)).astype(np.float16))
 
 
+def test_conv1x1_small_forward_backward():
+    """The head's float32 1x1 convolution (32 -> 3) and its backward against numpy."""
+    import torch
+    r = _rng(42)
+    x = r.normal(size=(3, 7, 9, 32))
+    w = r.normal(size=(3, 32))
+    b = r.normal(size=(3,))
+    y = torch.empty((3, 7, 9, 3), device="cuda")
+    S.smrt_nn_conv1x1_small(_t(x), _t(w), _t(b), y)
+    assert np.abs(_np(y) - (x @ w.T + b)).max() < 1e-4
+    dy = r.normal(size=(3, 7, 9, 3))
+    dx = torch.empty((3, 7, 9, 32), device="cuda")
+    dw = _t(np.ones((3, 32)))
+    db = _t(np.ones(3))
+    S.smrt_nn_conv1x1_small_bwd(_t(dy), _t(x), _t(w), dx, dw, db)
+    assert np.abs(_np(dx) - dy @ w).max() < 1e-4
+    assert np.abs(_np(dw) - (1 + dy.reshape(-1, 3).T @ x.reshape(-1, 32))).max() < 1e-3
+    assert np.abs(_np(db) - (1 + dy.reshape(-1, 3).sum(axis=0))).max() < 1e-4
+
+
 def test_upcat_and_its_adjoint():
     import torch
     r = _rng(41)
