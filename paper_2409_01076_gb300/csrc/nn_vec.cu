@@ -215,6 +215,13 @@ __global__ void add_vec(const float *a, const float *b, int n4, float *y)
     }
 }
 
+__device__ __forceinline__ float warp_sum(float v)
+{
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // 1x1 convolution with few outputs (the network's head), float32 on the CUDA cores: a product of
 // COUT x C per pixel is far too narrow for the tensor cores and is bound by reading x.
 // Forward: y[p][o] = sum_c x[p][c] w[o][c] + b[o].  Thread: one pixel.
@@ -292,14 +299,20 @@ conv1x1_small_bwd(const float *__restrict__ dy, const float *__restrict__ x, int
             if (dxp) stv<4>(dxp + 4 * q, d);
         }
     }
+    // warp sums first (shuffles), then one shared-memory atomic per warp and entry
+    const bool lead = (threadIdx.x & 31) == 0;
     #pragma unroll
     for (int o = 0; o < COUT; ++o) {
-        atomicAdd(&sacc[COUT * C + o], gb[o]);
+        const float b = warp_sum(gb[o]);
+        if (lead) atomicAdd(&sacc[COUT * C + o], b);
         #pragma unroll
         for (int q = 0; q < 16; ++q) {
             if (4 * q >= C) break;
             #pragma unroll
-            for (int i = 0; i < 4; ++i) atomicAdd(&sacc[o * C + 4 * q + i], gw[o][q][i]);
+            for (int i = 0; i < 4; ++i) {
+                const float v = warp_sum(gw[o][q][i]);
+                if (lead) atomicAdd(&sacc[o * C + 4 * q + i], v);
+            }
         }
     }
     __syncthreads();
@@ -417,7 +430,7 @@ cudaError_t small_conv1x1_bwd(const float *dy, const float *x, long long P, int 
                               float *dw, float *db, cudaStream_t s)
 {
     long long b = (P + 127) / 128;
-    if (b > 152LL * 4) b = 152LL * 4;
+    if (b > 152LL * 2) b = 152LL * 2;      // ~240 registers a thread: two blocks per SM, one wave
     const unsigned blocks = (unsigned)(b < 1 ? 1 : b);
     switch (cout) {
     case 1: conv1x1_small_bwd<1><<<blocks, 128, 0, s>>>(dy, x, (int)P, C, w, dx, dw, db); break;
