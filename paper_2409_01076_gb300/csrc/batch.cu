@@ -299,15 +299,15 @@ size_t cav_bytes()
 }
 
 template <int PREC>
-StepGeom geom_for(int shape, int nx, int ny)
+StepGeom geom_for(int shape, int nx, int ny, bool edge_in)
 {
     Shape sh = Shapes<PREC>::at(shape);
-    if (sh.vec == 4 && sh.bx == 128) return step_geom<4, 128>(nx, ny);
-    if (sh.vec == 4 && sh.bx == 64) return step_geom<4, 64>(nx, ny);
-    if (sh.vec == 4 && sh.bx == 256) return step_geom<4, 256>(nx, ny);
-    if (sh.vec == 2 && sh.bx == 128) return step_geom<2, 128>(nx, ny);
-    if (sh.vec == 2 && sh.bx == 64) return step_geom<2, 64>(nx, ny);
-    return step_geom<1, 128>(nx, ny);
+    if (sh.vec == 4 && sh.bx == 128) return step_geom<4, 128>(nx, ny, edge_in);
+    if (sh.vec == 4 && sh.bx == 64) return step_geom<4, 64>(nx, ny, edge_in);
+    if (sh.vec == 4 && sh.bx == 256) return step_geom<4, 256>(nx, ny, edge_in);
+    if (sh.vec == 2 && sh.bx == 128) return step_geom<2, 128>(nx, ny, edge_in);
+    if (sh.vec == 2 && sh.bx == 64) return step_geom<2, 64>(nx, ny, edge_in);
+    return step_geom<1, 128>(nx, ny, edge_in);
 }
 
 template <int PREC>
@@ -452,11 +452,11 @@ int upload_lists(smrt_batch_t *b)
         smrt::StepGeom g;
         int nb;
         if (b->prec == SMRT_PREC_F64) {
-            g = smrt::geom_for<SMRT_PREC_F64>(b->shape, L.nx, L.ny);
+            g = smrt::geom_for<SMRT_PREC_F64>(b->shape, L.nx, L.ny, b->layout == SMRT_LAYOUT_AB);
             nb = smrt::step_blocks<SMRT_PREC_F64>(b->shape, g);
             smrt::fill_cav<SMRT_PREC_F64>(&b->h_cav[cb * k], hp, g, L.offset, L.uoff);
         } else {
-            g = smrt::geom_for<SMRT_PREC_F32>(b->shape, L.nx, L.ny);
+            g = smrt::geom_for<SMRT_PREC_F32>(b->shape, L.nx, L.ny, b->layout == SMRT_LAYOUT_AB);
             nb = smrt::step_blocks<SMRT_PREC_F32>(b->shape, g);
             smrt::fill_cav<SMRT_PREC_F32>(&b->h_cav[cb * k], hp, g, L.offset, L.uoff);
         }
@@ -610,8 +610,10 @@ int smrt_batch_create(int count, const int *nx, const int *ny, const double *tau
         long long w = 0;
         for (const Lat &L : b->lat)
             w += precision == SMRT_PREC_F64
-                     ? smrt::step_blocks<SMRT_PREC_F64>(s, smrt::geom_for<SMRT_PREC_F64>(s, L.nx, L.ny))
-                     : smrt::step_blocks<SMRT_PREC_F32>(s, smrt::geom_for<SMRT_PREC_F32>(s, L.nx, L.ny));
+                     ? smrt::step_blocks<SMRT_PREC_F64>(s, smrt::geom_for<SMRT_PREC_F64>(s, L.nx, L.ny,
+                                                                                         layout == SMRT_LAYOUT_AB))
+                     : smrt::step_blocks<SMRT_PREC_F32>(s, smrt::geom_for<SMRT_PREC_F32>(s, L.nx, L.ny,
+                                                                                         layout == SMRT_LAYOUT_AB));
         if (w > b->max_work) b->max_work = w;
     }
     if (b->max_work >= (1LL << 31)) {

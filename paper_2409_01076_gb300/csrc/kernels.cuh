@@ -11,6 +11,8 @@
 //     shuffle (one extra scalar load at each warp edge); no boundary logic;
 //   - band blocks: the remaining ring of nodes (rows 0 and ny-1, columns [0, L)
 //     and [R, nx)), one node per thread, with the full boundary resolution.
+//     In the two-buffer layout L = 0 and R = nx (when nx % VEC == 0): the edge
+//     column groups run in the vector path and fix up their boundary pulls.
 #pragma once
 
 #include "d2q9.cuh"
@@ -31,12 +33,21 @@ struct StepGeom {
     long long n_edge;    // band nodes
 };
 
+// edge_in (the two-buffer layout only): the first and, when nx % VEC == 0, the last VEC-wide
+// column group of every interior row run in the vector path too; the one or two populations of
+// the edge node that cross the x boundary are then pulled through the full boundary resolution by
+// that node's own lane.  (The in-place layout's odd step also stores across the boundary, so it
+// keeps those columns in the band.)
 template <int VEC, int BX>
-inline StepGeom step_geom(int nx, int ny)
+inline StepGeom step_geom(int nx, int ny, bool edge_in)
 {
     StepGeom g;
     int L = VEC < nx ? VEC : nx;
     int R = ((nx - 1) / VEC) * VEC;
+    if (edge_in && nx >= 2 * VEC) {
+        L = 0;
+        R = (nx / VEC) * VEC;
+    }
     if (R < L) R = L;
     g.L = L;
     g.R = R;
@@ -226,6 +237,31 @@ __device__ __forceinline__ void step_block(const typename Prec<PREC>::R *src, ty
         load_row<PREC, VEC>(rp, i0, s, lane, loader, p.nx, vals);
         #pragma unroll
         for (int k = 0; k < VEC; ++k) g[k][a] = vals[k];
+    }
+    if (MODE == MODE_AB && geo.L == 0 && active) {
+        // edge groups: the populations pulled across the left (a = 1, 5, 8) or right (a = 3, 6, 7)
+        // boundary, through the full resolution (wall, moving wall or periodic wrap)
+        using P = Prec<PREC>;
+        if (i0 == 0) {
+            #pragma unroll
+            for (int a = 1; a < 9; ++a) {
+                if (ex(a) != 1) continue;
+                const Loc L = pull_loc<MODE>(p, a, 0, j);
+                C v = P::to_c(src[at(p.plane, p.pitch, L.plane, L.j, L.i)]);
+                if (L.side >= 0) v += p.corr[L.side][a];
+                g[0][a] = v;
+            }
+        }
+        if (i0 + VEC == p.nx) {
+            #pragma unroll
+            for (int a = 1; a < 9; ++a) {
+                if (ex(a) != -1) continue;
+                const Loc L = pull_loc<MODE>(p, a, p.nx - 1, j);
+                C v = P::to_c(src[at(p.plane, p.pitch, L.plane, L.j, L.i)]);
+                if (L.side >= 0) v += p.corr[L.side][a];
+                g[VEC - 1][a] = v;
+            }
+        }
     }
     bool ok = true;
     #pragma unroll
@@ -517,7 +553,7 @@ cudaError_t launch_step_km(const void *src, void *dst, const HostParams &hp, cud
     using R = typename P::R;
     constexpr int VEC = Tune<PREC>::VEC, BX = Tune<PREC>::BX;
     const Params<typename P::C> p = make_params<typename P::C>(hp);
-    const StepGeom geo = step_geom<VEC, BX>(hp.nx, hp.ny);
+    const StepGeom geo = step_geom<VEC, BX>(hp.nx, hp.ny, MODE == MODE_AB);
     const long long edge_blocks = (geo.n_edge + BX - 1) / BX;
     const long long blocks = (long long)geo.n_int_blocks + edge_blocks;
     if (blocks <= 0) return cudaSuccess;
