@@ -97,6 +97,15 @@ SMRT_API int smrt_nn_pack3(const void *w, int cout, int C, void *wp, void *strea
 SMRT_API int smrt_nn_conv3_tma(const void *xb, int N, int H, int W, int C, const void *wp, int cout, float alpha,
                                float beta, float *y, int ldy, int *err, void *stream);
 
+/* smrt_nn_conv3_tma with the bias and the activation in its epilogue (the float32 convolution output
+ * never goes to memory): v = conv + bias[o], z = v, a = SiLU(v) (act) or v, ab = half(a) blocked,
+ * each written when its pointer is not NULL (z, a: N*H*W rows of cout float32; ab: the blocked layout
+ * with cout channels; at least one output).  cout % 8 == 0; outputs 16-byte aligned.  The values
+ * equal smrt_nn_conv3_tma followed by smrt_nn_bias_act_blocked bit for bit. */
+SMRT_API int smrt_nn_conv3_tma_bias_act(const void *xb, int N, int H, int W, int C, const void *wp, int cout,
+                                        const float *bias, int act, float *z, float *a, void *ab, int *err,
+                                        void *stream);
+
 /* Weight gradient of the same convolution, ACCUMULATED into gw (cout rows of ldg >= 9C float32):
  *   gw[o][tap*C + c] += alpha * sum_p x[n][yy+ky-1][xx+kx-1][c] * dz[p][o]
  * with x and dz both blocked half (xb: C channels, dzb: cout channels, C % 8 == 0, cout % 8 == 0).

@@ -58,6 +58,17 @@ static_assert(kTileRows * kTilePx == 128, "M = 128");
 
 int tile_n(int cout) { return cout <= 32 ? 32 : cout <= 64 ? 64 : 128; }
 
+// Fused epilogue of the forward convolution (on != 0): v = acc + bias[o]; z = v; a = SiLU(v) (or v);
+// ab = half(a) in the blocked layout.  Any of z, a, ab may be null; cout % 8 == 0.
+struct Epi {
+    const float *bias;
+    float *z, *a;
+    __half *ab;
+    int act, on;
+};
+
+__device__ __forceinline__ float sigm(float v) { return 1.0f / (1.0f + expf(-v)); }
+
 template <int TN>
 constexpr int fwd_stage_bytes()
 {
@@ -213,7 +224,8 @@ __device__ __forceinline__ void teardown(uint32_t tmem)
 template <int TN>
 __global__ void __launch_bounds__(128)
 conv3_tma_kernel(const __grid_constant__ CUtensorMap tmx, const __half *__restrict__ wp, int H, int W, int C,
-                 int cout, int ntn, int nstages, float alpha, float beta, float *y, int ldy, int vec_y, int *err)
+                 int cout, int ntn, int nstages, float alpha, float beta, float *y, int ldy, int vec_y, int *err,
+                 Epi epi)
 {
     extern __shared__ unsigned char dyn_raw[];
     __shared__ __align__(8) unsigned long long full[kFwdStages], empty[kFwdStages], done;
@@ -268,13 +280,46 @@ conv3_tma_kernel(const __grid_constant__ CUtensorMap tmx, const __half *__restri
         const int m = warp * 32 + lane;
         const int yy = y0 + (m >> 3), xx = x0 + (m & 7);
         const bool valid = yy < H && xx < W;
-        float *yrow = y + ((size_t)((size_t)img * H + (valid ? yy : 0)) * W + (valid ? xx : 0)) * ldy;
+        const size_t pix = (size_t)((size_t)img * H + (valid ? yy : 0)) * W + (valid ? xx : 0);
+        float *yrow = epi.on ? nullptr : y + pix * ldy;
         #pragma unroll 1
         for (int c = 0; c < TN; c += 32) {
             uint32_t r[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, r);
             if (!valid) continue;
             const int col0 = n0 + c;
+            if (epi.on) {
+                #pragma unroll
+                for (int j = 0; j < 32; j += 8) {
+                    if (col0 + j >= cout) break;
+                    float v[8];
+                    #pragma unroll
+                    for (int e = 0; e < 8; ++e) v[e] = __uint_as_float(r[j + e]) + epi.bias[col0 + j + e];
+                    if (epi.z) {
+                        float4 *q = reinterpret_cast<float4 *>(epi.z + pix * cout + col0 + j);
+                        q[0] = make_float4(v[0], v[1], v[2], v[3]);
+                        q[1] = make_float4(v[4], v[5], v[6], v[7]);
+                    }
+                    if (epi.act) {
+                        #pragma unroll
+                        for (int e = 0; e < 8; ++e) v[e] = v[e] * sigm(v[e]);
+                    }
+                    if (epi.a) {
+                        float4 *q = reinterpret_cast<float4 *>(epi.a + pix * cout + col0 + j);
+                        q[0] = make_float4(v[0], v[1], v[2], v[3]);
+                        q[1] = make_float4(v[4], v[5], v[6], v[7]);
+                    }
+                    if (epi.ab) {
+                        __half2 h[4];
+                        #pragma unroll
+                        for (int e = 0; e < 4; ++e) h[e] = __floats2half2_rn(v[2 * e], v[2 * e + 1]);
+                        const size_t g = (size_t)(col0 + j) / 8, G = (size_t)cout / 8;
+                        *reinterpret_cast<uint4 *>(epi.ab + (((size_t)img * G + g) * H * W + (size_t)yy * W + xx) * 8) =
+                            *reinterpret_cast<uint4 *>(h);
+                    }
+                }
+                continue;
+            }
             if (vec_y && col0 + 32 <= cout) {
                 #pragma unroll
                 for (int j = 0; j < 32; j += 4) {
@@ -486,7 +531,7 @@ bool blocked_args_ok(const void *p, int N, int H, int W, int C)
 
 template <int TN>
 cudaError_t launch_conv3_tma(const CUtensorMap &tmx, const __half *wp, int N, int H, int W, int C, int cout,
-                             float alpha, float beta, float *y, int ldy, int *err, cudaStream_t s)
+                             float alpha, float beta, float *y, int ldy, int *err, cudaStream_t s, const Epi &epi)
 {
     const int ntn = (cout + TN - 1) / TN;
     const int nchunks = C / kChunk;
@@ -505,7 +550,7 @@ cudaError_t launch_conv3_tma(const CUtensorMap &tmx, const __half *wp, int N, in
         attr_set = true;
     }
     conv3_tma_kernel<TN><<<grid, 128, smem, s>>>(tmx, wp, H, W, C, cout, ntn, nstages, alpha, beta, y, ldy, vec_y,
-                                                 err);
+                                                 err, epi);
     return cudaGetLastError();
 }
 
@@ -562,10 +607,39 @@ extern "C" int smrt_nn_conv3_tma(const void *xb, int N, int H, int W, int C, con
     const __half *w = (const __half *)wp;
     cudaError_t e;
     const int TN = tile_n(cout);
-    if (TN == 32) e = launch_conv3_tma<32>(tmx, w, N, H, W, C, cout, alpha, beta, y, ldy, err, s);
-    else if (TN == 64) e = launch_conv3_tma<64>(tmx, w, N, H, W, C, cout, alpha, beta, y, ldy, err, s);
-    else e = launch_conv3_tma<128>(tmx, w, N, H, W, C, cout, alpha, beta, y, ldy, err, s);
+    const Epi plain{nullptr, nullptr, nullptr, nullptr, 0, 0};
+    if (TN == 32) e = launch_conv3_tma<32>(tmx, w, N, H, W, C, cout, alpha, beta, y, ldy, err, s, plain);
+    else if (TN == 64) e = launch_conv3_tma<64>(tmx, w, N, H, W, C, cout, alpha, beta, y, ldy, err, s, plain);
+    else e = launch_conv3_tma<128>(tmx, w, N, H, W, C, cout, alpha, beta, y, ldy, err, s, plain);
     if (e != cudaSuccess) return tma_fail(SMRT_ERR_CUDA, "smrt_nn_conv3_tma: %s", cudaGetErrorString(e));
+    return SMRT_OK;
+}
+
+extern "C" int smrt_nn_conv3_tma_bias_act(const void *xb, int N, int H, int W, int C, const void *wp, int cout,
+                                          const float *bias, int act, float *z, float *a, void *ab, int *err,
+                                          void *stream)
+{
+    const uintptr_t al = reinterpret_cast<uintptr_t>(z) | reinterpret_cast<uintptr_t>(a) |
+                         reinterpret_cast<uintptr_t>(ab);
+    if (!blocked_args_ok(xb, N, H, W, C) || C % kChunk != 0 || !wp || !bias || cout < 8 || cout % 8 != 0 ||
+        (!z && !a && !ab) || (al & 15) || (reinterpret_cast<uintptr_t>(wp) & 15) != 0 ||
+        (H + kTileRows - 1) / kTileRows > 65535 || (long long)N * ((cout + tile_n(cout) - 1) / tile_n(cout)) > 65535)
+        return tma_fail(SMRT_ERR_ARG,
+                        "smrt_nn_conv3_tma_bias_act: bad arguments (N %d H %d W %d C %d cout %d; C %% 16 == 0, "
+                        "cout %% 8 == 0, 16-byte aligned outputs, at least one output)", N, H, W, C, cout);
+    CUtensorMap tmx;
+    CUresult r = blocked_map(&tmx, xb, N, H, W, C, kHaloPx, kHaloRows, 2);
+    if (r != CUDA_SUCCESS)
+        return tma_fail(SMRT_ERR_CUDA, "smrt_nn_conv3_tma_bias_act: tensor map rejected (%d)", (int)r);
+    cudaStream_t s = (cudaStream_t)stream;
+    const __half *w = (const __half *)wp;
+    const Epi epi{bias, z, a, (__half *)ab, act, 1};
+    cudaError_t e;
+    const int TN = tile_n(cout);
+    if (TN == 32) e = launch_conv3_tma<32>(tmx, w, N, H, W, C, cout, 1.0f, 0.0f, nullptr, cout, err, s, epi);
+    else if (TN == 64) e = launch_conv3_tma<64>(tmx, w, N, H, W, C, cout, 1.0f, 0.0f, nullptr, cout, err, s, epi);
+    else e = launch_conv3_tma<128>(tmx, w, N, H, W, C, cout, 1.0f, 0.0f, nullptr, cout, err, s, epi);
+    if (e != cudaSuccess) return tma_fail(SMRT_ERR_CUDA, "smrt_nn_conv3_tma_bias_act: %s", cudaGetErrorString(e));
     return SMRT_OK;
 }
 

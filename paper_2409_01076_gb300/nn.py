@@ -66,6 +66,14 @@ def smrt_nn_conv3_tma(xb, nhwc, wp, y, cout, alpha=1.0, beta=0.0, err=None):
                                          float(beta), _p(y), int(y.shape[-1]), _p(err), _s()))
 
 
+def smrt_nn_conv3_tma_bias_act(xb, nhwc, wp, cout, bias, act, z, a, ab, err=None):
+    """Forward convolution with bias and activation in the epilogue; z, a: N*H*W rows of cout float32 or
+    None; ab: blocked halves or None."""
+    n, h, w, c = nhwc
+    _check(_lib.load().smrt_nn_conv3_tma_bias_act(_p(xb), int(n), int(h), int(w), int(c), _p(wp), int(cout),
+                                                  _p(bias), int(act), _p(z), _p(a), _p(ab), _p(err), _s()))
+
+
 def smrt_nn_conv3_wgrad_tma(xb, nhwc, dzb, cout, gw, alpha=1.0, err=None):
     """gw (cout, ldg >= 9C) float32 += alpha * weight gradient from blocked half x and dz."""
     n, h, w, c = nhwc

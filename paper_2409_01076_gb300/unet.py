@@ -156,6 +156,17 @@ class UNet:
             if xb is None:
                 xb = t.empty(rows * ci, dtype=t.float16, device=self.device)
                 K.smrt_nn_to_half_blocked(inp.f, xb)
+            if co % 8 == 0:
+                # bias and SiLU in the convolution's epilogue: writes z, a and / or the blocked halves
+                want_b = out_b and self._blocked_ok(co)
+                z = t.empty_like(y) if (act and cache is not None) else None
+                a = y if (out_f or not want_b) else None
+                ab = t.empty(rows * co, dtype=t.float16, device=self.device) if want_b else None
+                K.smrt_nn_conv3_tma_bias_act(xb, inp.shape, self._wp[name], co, self.params[name + ".b"], act, z, a,
+                                             ab, self._gemm_err)
+                if cache is not None:
+                    cache[name] = (None, z, inp.f, xb, inp.shape)
+                return _Act(a, ab, (n, h, w, co))
             K.smrt_nn_conv3_tma(xb, inp.shape, self._wp[name], y, co, 1.0, 0.0, self._gemm_err)
         elif self._implicit(k, ci):
             # implicit GEMM: the A tiles are gathered from x, no im2col matrix is built

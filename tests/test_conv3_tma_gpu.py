@@ -107,6 +107,33 @@ def test_conv3_tma_agrees_with_the_gather_kernel():
     assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("act", [1, 0])
+def test_conv3_tma_bias_act_equals_the_unfused_pair_bitwise(act):
+    """Bias and SiLU in the convolution's epilogue give exactly what smrt_nn_conv3_tma followed by
+    smrt_nn_bias_act_blocked gives (z, a and the blocked halves), on ragged tiles and two N tiles."""
+    import torch
+    n, h, w, C, cout = 2, 21, 13, 32, 136
+    r = _rng(90 + act)
+    x = r.normal(size=(n, h, w, C)).astype(np.float16)
+    wt = torch.tensor(r.normal(size=(cout, 9 * C)).astype(np.float16), device="cuda")
+    bias = torch.tensor(r.normal(size=cout).astype(np.float32), device="cuda")
+    xb = torch.tensor(_blocked(x), device="cuda")
+    wp = torch.empty(S.smrt_nn_pack3_halves(cout, C), dtype=torch.float16, device="cuda")
+    S.smrt_nn_pack3(wt, C, wp)
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    y = torch.empty((n, h, w, cout), device="cuda")
+    S.smrt_nn_conv3_tma(xb, (n, h, w, C), wp, y, cout, 1.0, 0.0, err)
+    z1, a1 = torch.empty_like(y), torch.empty_like(y)
+    ab1 = torch.empty(y.numel(), dtype=torch.float16, device="cuda")
+    S.smrt_nn_bias_act_blocked(y, bias, act, z1, a1, ab1)
+    z2, a2 = torch.empty_like(y), torch.empty_like(y)
+    ab2 = torch.empty(y.numel(), dtype=torch.float16, device="cuda")
+    S.smrt_nn_conv3_tma_bias_act(xb, (n, h, w, C), wp, cout, bias, act, z2, a2, ab2, err)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    assert torch.equal(z1, z2) and torch.equal(a1, a2) and torch.equal(ab1, ab2)
+
+
 def _wgrad(n, h, w, C, cout, alpha, seed):
     import torch
     r = _rng(seed)
