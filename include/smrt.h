@@ -244,10 +244,12 @@ SMRT_API int smrt_batch_create(int count, const int *nx, const int *ny, const do
 SMRT_API int smrt_batch_set_stream(smrt_batch_t *b, void *stream);
 
 /* Times each candidate tile shape of the work-list kernel (nodes per thread x
- * threads per block, with or without a 64-register bound; FP32 storage: 5
- * candidates, FP64: 4) on `steps` steps of this batch, run on a copy of the state
- * so no lattice advances, and keeps the fastest; *choice (may be NULL) receives
- * its index.  Allocates one scratch copy of the populations for the duration. */
+ * threads per block, with or without a 64-register bound, each without (index k)
+ * and with (index k + 5 for FP32 storage, k + 4 for FP64) the edge column groups
+ * of the two-buffer layout in the vector path; FP32: 10 candidates, FP64: 8) on
+ * `steps` steps of this batch, run on a copy of the state so no lattice advances,
+ * and keeps the fastest; *choice (may be NULL) receives its index.  Allocates one
+ * scratch copy of the populations for the duration. */
 SMRT_API int smrt_batch_autotune(smrt_batch_t *b, int steps, int *choice);
 
 /* Selects tile shape `shape` (an index as returned by smrt_batch_autotune) without

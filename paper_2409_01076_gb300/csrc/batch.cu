@@ -51,7 +51,9 @@ __device__ __forceinline__ void cp_async_wait_all()
 
 // CAP bounds the kernel to 64 registers (1024 resident threads per SM); without it the
 // compiler takes what the step needs and fewer blocks are resident.
-template <int PREC, int KIND, int MODE, int VEC, int BX, bool CAP>
+// EDGE: the two-buffer step also runs the edge column groups in the vector path (their geometry
+// must say so); without it those columns stay in the band and the vector path carries no edge code.
+template <int PREC, int KIND, int MODE, int VEC, int BX, bool CAP, bool EDGE>
 __global__ void __launch_bounds__(BX, CAP ? 1024 / BX : 1)
 batch_step_kernel(const typename Prec<PREC>::R *src, typename Prec<PREC>::R *dst,
                   const BatchCav<typename Prec<PREC>::C> *__restrict__ cav, const int2 *__restrict__ work,
@@ -87,7 +89,7 @@ batch_step_kernel(const typename Prec<PREC>::R *src, typename Prec<PREC>::R *dst
             for (int k = threadIdx.x; k < kWords; k += BX) cp_async8(&rec[buf ^ 1][k], g + k);
         }
         const Cav &r = *reinterpret_cast<const Cav *>(rec[buf]);
-        step_block<PREC, KIND, MODE, VEC, BX>(src + r.offset, dst + r.offset, r.p, r.geo, w.y);
+        step_block<PREC, KIND, MODE, VEC, BX, EDGE>(src + r.offset, dst + r.offset, r.p, r.geo, w.y);
         if (!next) break;
         if (swap) {
             cp_async_wait_all();
@@ -184,34 +186,45 @@ batch_finish_kernel(const int *__restrict__ act, const int *__restrict__ rpre, c
 
 // ---- launch-shape candidates (the autotuner's search space) ----------------------
 
+// A candidate is a base shape (nodes per thread, threads per block, 64-register bound) without
+// (index k) or with (index k + nbase) the edge column groups in the vector path.  Measured on one
+// GB300: the edge variant is faster on batches of lattices up to ~1024 wide (256^2: +20 %), the
+// plain one on batches of 4096^2 lattices (the edge code costs the vector path a few per cent there).
 struct Shape {
     int vec, bx;
     bool cap;   // 64-register bound
+    bool edge;  // edge column groups in the vector path (two-buffer layout)
 };
 template <int PREC> struct Shapes;
 template <> struct Shapes<SMRT_PREC_F32> {
-    static constexpr int n = 5;
+    static constexpr int nbase = 5, n = 2 * nbase;
     static Shape at(int k)
     {
-        const Shape s[n] = {{4, 128, true}, {4, 64, true}, {4, 256, true}, {2, 128, true}, {4, 128, false}};
-        return s[k];
+        const Shape s[nbase] = {{4, 128, true, false}, {4, 64, true, false}, {4, 256, true, false},
+                                {2, 128, true, false}, {4, 128, false, false}};
+        Shape r = s[k % nbase];
+        r.edge = k >= nbase;
+        return r;
     }
 };
 template <> struct Shapes<SMRT_PREC_F64> {
-    static constexpr int n = 4;
+    static constexpr int nbase = 4, n = 2 * nbase;
     static Shape at(int k)
     {
-        const Shape s[n] = {{2, 128, true}, {2, 64, true}, {1, 128, true}, {2, 128, false}};
-        return s[k];
+        const Shape s[nbase] = {{2, 128, true, false}, {2, 64, true, false}, {1, 128, true, false},
+                                {2, 128, false, false}};
+        Shape r = s[k % nbase];
+        r.edge = k >= nbase;
+        return r;
     }
 };
 
-template <int PREC, int KIND, int MODE, int VEC, int BX, bool CAP = true>
+template <int PREC, int KIND, int MODE, int VEC, int BX, bool CAP = true, bool EDGE = false>
 cudaError_t launch_batch_step_shape(const void *src, void *dst, const void *cav, const int2 *work,
                                     const int *counts, int sms, cudaStream_t s)
 {
     using P = Prec<PREC>;
-    auto kern = batch_step_kernel<PREC, KIND, MODE, VEC, BX, CAP>;
+    auto kern = batch_step_kernel<PREC, KIND, MODE, VEC, BX, CAP, EDGE>;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BX, 0);
     if (e != cudaSuccess) return e;
@@ -225,6 +238,8 @@ template <int PREC, int KIND, int MODE>
 cudaError_t launch_batch_step_m(int shape, const void *src, void *dst, const void *cav, const int2 *work,
                                 const int *counts, int sms, cudaStream_t s)
 {
+    // the edge variants exist for the two-buffer step only (the in-place step never takes that path)
+    constexpr bool E = MODE == MODE_AB;
     if constexpr (PREC == SMRT_PREC_F32) {
         switch (shape) {
         case 0: return launch_batch_step_shape<PREC, KIND, MODE, 4, 128>(src, dst, cav, work, counts, sms, s);
@@ -232,6 +247,11 @@ cudaError_t launch_batch_step_m(int shape, const void *src, void *dst, const voi
         case 2: return launch_batch_step_shape<PREC, KIND, MODE, 4, 256>(src, dst, cav, work, counts, sms, s);
         case 3: return launch_batch_step_shape<PREC, KIND, MODE, 2, 128>(src, dst, cav, work, counts, sms, s);
         case 4: return launch_batch_step_shape<PREC, KIND, MODE, 4, 128, false>(src, dst, cav, work, counts, sms, s);
+        case 5: return launch_batch_step_shape<PREC, KIND, MODE, 4, 128, true, E>(src, dst, cav, work, counts, sms, s);
+        case 6: return launch_batch_step_shape<PREC, KIND, MODE, 4, 64, true, E>(src, dst, cav, work, counts, sms, s);
+        case 7: return launch_batch_step_shape<PREC, KIND, MODE, 4, 256, true, E>(src, dst, cav, work, counts, sms, s);
+        case 8: return launch_batch_step_shape<PREC, KIND, MODE, 2, 128, true, E>(src, dst, cav, work, counts, sms, s);
+        case 9: return launch_batch_step_shape<PREC, KIND, MODE, 4, 128, false, E>(src, dst, cav, work, counts, sms, s);
         }
     } else {
         switch (shape) {
@@ -239,6 +259,10 @@ cudaError_t launch_batch_step_m(int shape, const void *src, void *dst, const voi
         case 1: return launch_batch_step_shape<PREC, KIND, MODE, 2, 64>(src, dst, cav, work, counts, sms, s);
         case 2: return launch_batch_step_shape<PREC, KIND, MODE, 1, 128>(src, dst, cav, work, counts, sms, s);
         case 3: return launch_batch_step_shape<PREC, KIND, MODE, 2, 128, false>(src, dst, cav, work, counts, sms, s);
+        case 4: return launch_batch_step_shape<PREC, KIND, MODE, 2, 128, true, E>(src, dst, cav, work, counts, sms, s);
+        case 5: return launch_batch_step_shape<PREC, KIND, MODE, 2, 64, true, E>(src, dst, cav, work, counts, sms, s);
+        case 6: return launch_batch_step_shape<PREC, KIND, MODE, 1, 128, true, E>(src, dst, cav, work, counts, sms, s);
+        case 7: return launch_batch_step_shape<PREC, KIND, MODE, 2, 128, false, E>(src, dst, cav, work, counts, sms, s);
         }
     }
     return cudaErrorInvalidValue;
@@ -302,6 +326,7 @@ template <int PREC>
 StepGeom geom_for(int shape, int nx, int ny, bool edge_in)
 {
     Shape sh = Shapes<PREC>::at(shape);
+    edge_in = edge_in && sh.edge;
     if (sh.vec == 4 && sh.bx == 128) return step_geom<4, 128>(nx, ny, edge_in);
     if (sh.vec == 4 && sh.bx == 64) return step_geom<4, 64>(nx, ny, edge_in);
     if (sh.vec == 4 && sh.bx == 256) return step_geom<4, 256>(nx, ny, edge_in);

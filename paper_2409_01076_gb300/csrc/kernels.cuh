@@ -10,10 +10,9 @@
 //     vector load and gets the +-1 column shift from its warp neighbour with a
 //     shuffle (one extra scalar load at each warp edge); no boundary logic;
 //   - band blocks: the remaining ring of nodes (rows 0 and ny-1, columns [0, L)
-//     and [R, nx)), one node per thread, with the full boundary resolution.  In
-//     the two-buffer layout the VEC-wide column groups of the band's interior
-//     rows go one group per thread instead (step_edge_group): aligned vector
-//     loads, lane-local shifts and one boundary pull per crossing direction.
+//     and [R, nx)), one node per thread, with the full boundary resolution.
+//     In the two-buffer layout L = 0 and R = nx (when nx % VEC == 0): the edge
+//     column groups run in the vector path and fix up their boundary pulls.
 #pragma once
 
 #include "d2q9.cuh"
@@ -31,19 +30,25 @@ struct StepGeom {
     int L, R;            // interior columns [L, R), multiples of VEC
     int bpr;             // interior blocks per row
     int n_int_blocks;    // bpr * (ny - 2)
-    long long n_edge;    // band items: n_grp column groups first, then single nodes
-    long long n_grp;     // column groups (interior rows x grp_per_row)
-    int grp_per_row;     // 0, 1 (the left group [0, VEC)) or 2 (and the right group [nx - VEC, nx))
+    long long n_edge;    // band nodes
 };
 
-// grp (two-buffer layout): the band's VEC-wide column groups of the interior rows are updated as
-// groups by one thread each.  The interior blocks are the same with or without it.
+// edge_in (the two-buffer layout only): the first and, when nx % VEC == 0, the last VEC-wide
+// column group of every interior row run in the vector path too; the one or two populations of
+// the edge node that cross the x boundary are then pulled through the full boundary resolution by
+// that node's own lane.  (The in-place layout's odd step also stores across the boundary, so it
+// keeps those columns in the band.)  A kernel built with step_block<..., EDGE = false> must be
+// given edge_in = false geometry.
 template <int VEC, int BX>
-inline StepGeom step_geom(int nx, int ny, bool grp)
+inline StepGeom step_geom(int nx, int ny, bool edge_in)
 {
     StepGeom g;
     int L = VEC < nx ? VEC : nx;
     int R = ((nx - 1) / VEC) * VEC;
+    if (edge_in && nx >= 2 * VEC) {
+        L = 0;
+        R = (nx / VEC) * VEC;
+    }
     if (R < L) R = L;
     g.L = L;
     g.R = R;
@@ -51,10 +56,8 @@ inline StepGeom step_geom(int nx, int ny, bool grp)
     int cols = R;                       // threads must cover [0, R) as loaders
     g.bpr = (R > L) ? (cols + BX * VEC - 1) / (BX * VEC) : 0;
     g.n_int_blocks = g.bpr * rows;
-    g.grp_per_row = (grp && VEC > 1 && nx >= 2 * VEC && L == VEC) ? (R == nx - VEC ? 2 : 1) : 0;
-    g.n_grp = (long long)rows * g.grp_per_row;
-    const long long bw = (long long)L + (long long)(nx - R) - (long long)g.grp_per_row * VEC;  // single-node columns
-    g.n_edge = g.n_grp + (ny >= 2 ? 2LL * nx : (long long)nx) + (long long)rows * bw;
+    long long bw = (long long)L + (long long)(nx - R);
+    g.n_edge = (ny >= 2 ? 2LL * nx : (long long)nx) + (long long)rows * bw;
     return g;
 }
 
@@ -188,74 +191,9 @@ __device__ __forceinline__ void step_node_generic(const typename Prec<PREC>::R *
     }
 }
 
-// The VEC nodes (i0 .. i0 + VEC - 1, j) of a band column group in the two-buffer layout, by one
-// thread: each population row is one aligned vector load, the +-1 column shift stays inside the
-// thread, and the node next to the x boundary (i0 == 0, or i0 + VEC == nx) pulls the population that
-// crosses it as pull_loc resolves that link -- periodic wrap (same plane, far column) or halfway
-// bounce-back (opposite plane, same node) plus the moving-wall term; rows 1..ny-2 cross no y
-// boundary.  The other group-edge neighbour is a plain in-row scalar load.  Results are those of
-// step_node_generic for each node, bit for bit.
-template <int PREC, int KIND, int VEC>
-__device__ __forceinline__ void step_edge_group(const typename Prec<PREC>::R *src, typename Prec<PREC>::R *dst,
-                                                const Params<typename Prec<PREC>::C> &p, int i0, int j)
-{
-    using P = Prec<PREC>;
-    using R = typename P::R;
-    using C = typename P::C;
-    const bool wrap = p.periodic_x != 0;
-    C g[VEC][9];
-    #pragma unroll
-    for (int a = 0; a < 9; ++a) {
-        const R *row = src + (size_t)a * (size_t)p.plane + (size_t)(j - ey(a)) * (size_t)p.pitch;
-        const RVec<R, VEC> v = *reinterpret_cast<const RVec<R, VEC> *>(row + i0);
-        C c[VEC];
-        #pragma unroll
-        for (int k = 0; k < VEC; ++k) c[k] = P::to_c(v.v[k]);
-        if (ex(a) == 0) {
-            #pragma unroll
-            for (int k = 0; k < VEC; ++k) g[k][a] = c[k];
-        } else if (ex(a) > 0) {                 // pulled from i - 1
-            #pragma unroll
-            for (int k = 1; k < VEC; ++k) g[k][a] = c[k - 1];
-            C e;
-            if (i0 > 0) {
-                e = P::to_c(row[i0 - 1]);
-            } else if (wrap) {
-                e = P::to_c(row[p.nx - 1]);
-            } else {
-                e = P::to_c(src[at(p.plane, p.pitch, opp(a), j, 0)]) + p.corr[SIDE_LEFT][a];
-            }
-            g[0][a] = e;
-        } else {                                // pulled from i + 1
-            #pragma unroll
-            for (int k = 0; k < VEC - 1; ++k) g[k][a] = c[k + 1];
-            C e;
-            if (i0 + VEC < p.nx) {
-                e = P::to_c(row[i0 + VEC]);
-            } else if (wrap) {
-                e = P::to_c(row[0]);
-            } else {
-                e = P::to_c(src[at(p.plane, p.pitch, opp(a), j, p.nx - 1)]) + p.corr[SIDE_RIGHT][a];
-            }
-            g[VEC - 1][a] = e;
-        }
-    }
-    bool ok = true;
-    #pragma unroll
-    for (int k = 0; k < VEC; ++k) ok &= collide<KIND>(p, g[k]);
-    if (!ok) atomicOr(p.flag, 1);
-    #pragma unroll
-    for (int a = 0; a < 9; ++a) {
-        RVec<R, VEC> o;
-        #pragma unroll
-        for (int k = 0; k < VEC; ++k) o.v[k] = P::to_r(g[k][a]);
-        *reinterpret_cast<RVec<R, VEC> *>(dst + (size_t)a * (size_t)p.plane + (size_t)j * (size_t)p.pitch + i0) = o;
-    }
-}
-
 // Block b of one lattice's step grid (interior block or band block), executed
 // by all BX threads of the calling block.
-template <int PREC, int KIND, int MODE, int VEC, int BX>
+template <int PREC, int KIND, int MODE, int VEC, int BX, bool EDGE = true>
 __device__ __forceinline__ void step_block(const typename Prec<PREC>::R *src, typename Prec<PREC>::R *dst,
                                            const Params<typename Prec<PREC>::C> &p, const StepGeom &geo, int b)
 {
@@ -263,16 +201,9 @@ __device__ __forceinline__ void step_block(const typename Prec<PREC>::R *src, ty
     const int tid = threadIdx.x;
 
     if (b >= geo.n_int_blocks) {
-        // ---- band: column groups (two-buffer layout), then one node per thread ----
+        // ---- band: one node per thread, full boundary handling ----
         long long e = (long long)(b - geo.n_int_blocks) * BX + tid;
         if (e >= geo.n_edge) return;
-        if (MODE == MODE_AB && VEC > 1 && e < geo.n_grp) {
-            const int jg = 1 + (int)(e / geo.grp_per_row);
-            const int side = (int)(e % geo.grp_per_row);
-            step_edge_group<PREC, KIND, VEC>(src, dst, p, side ? p.nx - VEC : 0, jg);
-            return;
-        }
-        e -= geo.n_grp;
         int i, j;
         if (e < p.nx) {
             i = (int)e; j = 0;
@@ -280,12 +211,10 @@ __device__ __forceinline__ void step_block(const typename Prec<PREC>::R *src, ty
             i = (int)(e - p.nx); j = p.ny - 1;
         } else {
             long long m = e - 2LL * p.nx;
-            const int lw = geo.grp_per_row > 0 ? 0 : geo.L;     // single-node columns left of R ...
-            const int rw = (p.nx - geo.R) - (geo.grp_per_row == 2 ? VEC : 0);   // ... and from R on
-            const int bw = lw + rw;
+            int bw = geo.L + (p.nx - geo.R);
             j = 1 + (int)(m / bw);
             int k = (int)(m % bw);
-            i = k < lw ? k : geo.R + (k - lw);
+            i = k < geo.L ? k : geo.R + (k - geo.L);
         }
         step_node_generic<PREC, KIND, MODE>(src, dst, p, i, j);
         return;
@@ -307,24 +236,33 @@ __device__ __forceinline__ void step_block(const typename Prec<PREC>::R *src, ty
         const typename Prec<PREC>::R *rp = src + (size_t)plane * (size_t)p.plane + (size_t)row * (size_t)p.pitch;
         C vals[VEC];
         load_row<PREC, VEC>(rp, i0, s, lane, loader, p.nx, vals);
-        if (MODE == MODE_AB && ex(a) != 0 && geo.L == 0) {
-            // edge group of the two-buffer layout: the population of the x-edge node pulled across
-            // the left (e_x = +1) or right (e_x = -1) boundary.  Rows 1..ny-2 cross no y boundary, so
-            // it is the periodic wrap (same plane, far column) or halfway bounce-back (opposite plane,
-            // same node) plus the moving-wall term -- what pull_loc resolves for that link.
-            const int k = ex(a) > 0 ? 0 : VEC - 1;
-            if (active && (ex(a) > 0 ? i0 == 0 : i0 + VEC == p.nx)) {
-                const bool wrap = p.periodic_x != 0;
-                const int side = ex(a) > 0 ? SIDE_LEFT : SIDE_RIGHT;
-                const int pl = wrap ? a : opp(a), rr = wrap ? j - ey(a) : j;
-                const int cc = wrap ? (ex(a) > 0 ? p.nx - 1 : 0) : i0 + k;
-                C v = Prec<PREC>::to_c(src[at(p.plane, p.pitch, pl, rr, cc)]);
-                if (!wrap) v += p.corr[side][a];
-                vals[k] = v;
-            }
-        }
         #pragma unroll
         for (int k = 0; k < VEC; ++k) g[k][a] = vals[k];
+    }
+    if (EDGE && MODE == MODE_AB && geo.L == 0 && active) {
+        // edge groups: the populations pulled across the left (a = 1, 5, 8) or right (a = 3, 6, 7)
+        // boundary, through the full resolution (wall, moving wall or periodic wrap)
+        using P = Prec<PREC>;
+        if (i0 == 0) {
+            #pragma unroll
+            for (int a = 1; a < 9; ++a) {
+                if (ex(a) != 1) continue;
+                const Loc L = pull_loc<MODE>(p, a, 0, j);
+                C v = P::to_c(src[at(p.plane, p.pitch, L.plane, L.j, L.i)]);
+                if (L.side >= 0) v += p.corr[L.side][a];
+                g[0][a] = v;
+            }
+        }
+        if (i0 + VEC == p.nx) {
+            #pragma unroll
+            for (int a = 1; a < 9; ++a) {
+                if (ex(a) != -1) continue;
+                const Loc L = pull_loc<MODE>(p, a, p.nx - 1, j);
+                C v = P::to_c(src[at(p.plane, p.pitch, L.plane, L.j, L.i)]);
+                if (L.side >= 0) v += p.corr[L.side][a];
+                g[VEC - 1][a] = v;
+            }
+        }
     }
     bool ok = true;
     #pragma unroll
