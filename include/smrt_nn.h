@@ -74,6 +74,19 @@ SMRT_API int smrt_nn_conv3_tc(const float *x, int N, int H, int W, int C, const 
 SMRT_API int smrt_nn_to_half_blocked(const float *x, int N, int H, int W, int C, float scale, void *xb,
                                      void *stream);
 
+/* Zero-padded forms for a layer with few input channels (C < 16, e.g. the network's 3-channel input),
+ * so that it can run as a Cp- (or Cb-) channel TMA convolution whose extra channels are zero:
+ * smrt_nn_to_half_blocked_pad: xb (Cb channels, blocked) = half(scale * x) for c < C, 0 above; x is NHWC
+ *   float32 with C channels (any C >= 1), Cb >= C, Cb % 8 == 0, xb 16-byte aligned.
+ * smrt_nn_pad3: wh (cout x 9 Cp half) from 3x3 weights w (cout x 9 C float32, column tap*C + c):
+ *   wh[o][tap*Cp + c] = half(w[o][tap*C + c]) for c < C, 0 for C <= c < Cp.
+ * smrt_nn_unpad3_add: gw[o][tap*C + c] += gp[o][tap*Cp + c] for c < C (the weight gradient of the
+ *   padded layer folded back; the padded channels' gradient is exactly zero). */
+SMRT_API int smrt_nn_to_half_blocked_pad(const float *x, int N, int H, int W, int C, int Cb, float scale, void *xb,
+                                         void *stream);
+SMRT_API int smrt_nn_pad3(const float *w, int cout, int C, int Cp, void *wh, void *stream);
+SMRT_API int smrt_nn_unpad3_add(const float *gp, int cout, int C, int Cp, float *gw, void *stream);
+
 /* Halves that smrt_nn_pack3 writes for (cout, C): 9 * C * cout rounded up to whole output-channel
  * tiles (32 if cout <= 32, 64 if cout <= 64, else multiples of 128); -1 if C % 16 != 0 or cout < 1. */
 SMRT_API long long smrt_nn_pack3_halves(int cout, int C);

@@ -59,6 +59,10 @@ SIGNATURES = [
     ("smrt_nn_conv3_tc", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_int, ctypes.c_float,
                                  ctypes.c_float, c_void_p, c_int, c_void_p, c_void_p]),
     ("smrt_nn_to_half_blocked", c_int, [c_void_p, c_int, c_int, c_int, c_int, ctypes.c_float, c_void_p, c_void_p]),
+    ("smrt_nn_to_half_blocked_pad", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, ctypes.c_float, c_void_p,
+                                            c_void_p]),
+    ("smrt_nn_pad3", c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]),
+    ("smrt_nn_unpad3_add", c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]),
     ("smrt_nn_pack3_halves", c_longlong, [c_int, c_int]),
     ("smrt_nn_pack3", c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p]),
     ("smrt_nn_conv3_tma", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_int, ctypes.c_float,

@@ -457,6 +457,55 @@ __global__ void to_half_blocked_kernel(const float *__restrict__ x, int N, int H
     }
 }
 
+// xb (Cb channels, blocked) = half(scale * x) for c < C (x NHWC with C channels, any C), zero above.
+__global__ void to_half_blocked_pad_kernel(const float *__restrict__ x, int N, int H, int W, int C, int Cb,
+                                           float scale, __half *__restrict__ xb)
+{
+    const int G = Cb / 8;
+    const long long total = (long long)N * G * H * W;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int xx = (int)(i % W);
+        long long r = i / W;
+        const int yy = (int)(r % H);
+        r /= H;
+        const int g = (int)(r % G);
+        const int n = (int)(r / G);
+        const float *src = x + (((size_t)n * H + yy) * W + xx) * C;
+        __align__(16) __half h[8];
+        #pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int c = 8 * g + e;
+            h[e] = __float2half_rn(c < C ? scale * src[c] : 0.0f);
+        }
+        *reinterpret_cast<uint4 *>(xb + (size_t)i * 8) = *reinterpret_cast<const uint4 *>(h);
+    }
+}
+
+// wh[o][tap*Cp + c] = half(w[o][tap*C + c]) for c < C, 0 for C <= c < Cp.
+__global__ void pad3_kernel(const float *__restrict__ w, int cout, int C, int Cp, __half *__restrict__ wh)
+{
+    const long long total = 9LL * Cp * cout;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int o = (int)(i / (9 * Cp));
+        const int k = (int)(i % (9 * Cp)), tap = k / Cp, c = k % Cp;
+        wh[i] = __float2half_rn(c < C ? w[(size_t)o * 9 * C + (size_t)tap * C + c] : 0.0f);
+    }
+}
+
+// gw[o][tap*C + c] += gp[o][tap*Cp + c] for c < C.
+__global__ void unpad3_add_kernel(const float *__restrict__ gp, int cout, int C, int Cp, float *__restrict__ gw)
+{
+    const long long total = 9LL * C * cout;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int o = (int)(i / (9 * C));
+        const int k = (int)(i % (9 * C)), tap = k / C, c = k % C;
+        gw[i] += gp[(size_t)o * 9 * Cp + (size_t)tap * Cp + c];
+    }
+}
+
 // wp[(((nb * nchunks + chunk) * 18 + tap * 2 + q) * TN + r) * 8 + e] = w[nb*TN + r][tap*C + chunk*16 + q*8 + e]
 // (zero for output channels nb*TN + r >= cout).
 __global__ void pack3_kernel(const __half *__restrict__ w, int cout, int C, int TN, long long total,
@@ -588,6 +637,44 @@ extern "C" int smrt_nn_to_half_blocked(const float *x, int N, int H, int W, int 
     to_half_blocked_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(x, N, H, W, C, scale, (__half *)xb);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return tma_fail(SMRT_ERR_CUDA, "smrt_nn_to_half_blocked: %s", cudaGetErrorString(e));
+    return SMRT_OK;
+}
+
+extern "C" int smrt_nn_to_half_blocked_pad(const float *x, int N, int H, int W, int C, int Cb, float scale, void *xb,
+                                           void *stream)
+{
+    if (!x || C < 1 || Cb < C || !blocked_args_ok(xb, N, H, W, Cb))
+        return tma_fail(SMRT_ERR_ARG, "smrt_nn_to_half_blocked_pad: bad arguments (N %d H %d W %d C %d Cb %d; Cb >= C, "
+                        "Cb %% 8 == 0, xb 16-byte aligned)", N, H, W, C, Cb);
+    const long long total = (long long)N * (Cb / 8) * H * W;
+    const int blocks = (int)((total + 255) / 256 < 8192 ? (total + 255) / 256 : 8192);
+    to_half_blocked_pad_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(x, N, H, W, C, Cb, scale, (__half *)xb);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return tma_fail(SMRT_ERR_CUDA, "smrt_nn_to_half_blocked_pad: %s", cudaGetErrorString(e));
+    return SMRT_OK;
+}
+
+extern "C" int smrt_nn_pad3(const float *w, int cout, int C, int Cp, void *wh, void *stream)
+{
+    if (!w || !wh || cout < 1 || C < 1 || Cp < C || 9LL * Cp * cout > 0x7fffffffLL)
+        return tma_fail(SMRT_ERR_ARG, "smrt_nn_pad3: bad arguments (cout %d C %d Cp %d)", cout, C, Cp);
+    const long long total = 9LL * Cp * cout;
+    const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+    pad3_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(w, cout, C, Cp, (__half *)wh);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return tma_fail(SMRT_ERR_CUDA, "smrt_nn_pad3: %s", cudaGetErrorString(e));
+    return SMRT_OK;
+}
+
+extern "C" int smrt_nn_unpad3_add(const float *gp, int cout, int C, int Cp, float *gw, void *stream)
+{
+    if (!gp || !gw || cout < 1 || C < 1 || Cp < C || 9LL * Cp * cout > 0x7fffffffLL)
+        return tma_fail(SMRT_ERR_ARG, "smrt_nn_unpad3_add: bad arguments (cout %d C %d Cp %d)", cout, C, Cp);
+    const long long total = 9LL * C * cout;
+    const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+    unpad3_add_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(gp, cout, C, Cp, gw);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return tma_fail(SMRT_ERR_CUDA, "smrt_nn_unpad3_add: %s", cudaGetErrorString(e));
     return SMRT_OK;
 }
 

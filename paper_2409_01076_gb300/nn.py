@@ -50,6 +50,22 @@ def smrt_nn_to_half_blocked(x, xb, scale=1.0):
     _check(_lib.load().smrt_nn_to_half_blocked(_p(x), n, h, w, c, float(scale), _p(xb), _s()))
 
 
+def smrt_nn_to_half_blocked_pad(x, cb, xb, scale=1.0):
+    """x: (N, H, W, C) float32; xb: N*cb*H*W halves, blocked, channels C..cb-1 zero."""
+    n, h, w, c = x.shape
+    _check(_lib.load().smrt_nn_to_half_blocked_pad(_p(x), n, h, w, c, int(cb), float(scale), _p(xb), _s()))
+
+
+def smrt_nn_pad3(w, C, Cp, wh):
+    """w: (cout, 9C) float32; wh: (cout, 9Cp) half."""
+    _check(_lib.load().smrt_nn_pad3(_p(w), int(w.shape[0]), int(C), int(Cp), _p(wh), _s()))
+
+
+def smrt_nn_unpad3_add(gp, C, Cp, gw):
+    """gw (cout, 9C) float32 += the C-channel part of gp (cout, 9Cp)."""
+    _check(_lib.load().smrt_nn_unpad3_add(_p(gp), int(gw.shape[0]), int(C), int(Cp), _p(gw), _s()))
+
+
 def smrt_nn_pack3_halves(cout, C):
     return int(_lib.load().smrt_nn_pack3_halves(int(cout), int(C)))
 

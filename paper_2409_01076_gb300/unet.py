@@ -126,6 +126,11 @@ class UNet:
             if self._tma(k, ci):                # packed for the TMA convolution
                 self._wp[name] = t.empty(K.smrt_nn_pack3_halves(co, ci), dtype=t.float16, device=self.device)
                 K.smrt_nn_pack3(h, ci, self._wp[name])
+            elif self._tma_padded(spec):        # the input layer, zero-padded to 16 channels
+                hp = t.empty((co, 9 * 16), dtype=t.float16, device=self.device)
+                K.smrt_nn_pad3(w, ci, 16, hp)
+                self._wp[name] = t.empty(K.smrt_nn_pack3_halves(co, 16), dtype=t.float16, device=self.device)
+                K.smrt_nn_pack3(hp, 16, self._wp[name])
             if k == 3 and name != "enc1a":      # weights of the adjoint convolution (input gradient)
                 f = t.empty((ci, 9 * co), dtype=t.float16, device=self.device)
                 K.smrt_nn_flip3(w, f)
@@ -144,13 +149,18 @@ class UNet:
         kk = k * k * ci
         y = t.empty((n, h, w, co), dtype=t.float32, device=self.device)
         xb = col = None
+        if self._tma_padded(spec):
+            # the 3-channel input as a 16-channel TMA convolution whose extra channels (and weights) are zero
+            xb = t.empty(rows * 16, dtype=t.float16, device=self.device)
+            K.smrt_nn_to_half_blocked_pad(inp.f, 16, xb)
+            inp = _Act(inp.f, xb, (n, h, w, 16))
         if self._small_1x1(spec):
             # the head: a few float32 dot products per pixel, bias included
             K.smrt_nn_conv1x1_small(inp.f, self.params[name + ".w"], self.params[name + ".b"], y)
             if cache is not None:
                 cache[name] = (None, None, inp.f, None, inp.shape)
             return _Act(y, None, (n, h, w, co))
-        if self._tma(k, ci):
+        if self._tma(k, ci) or self._tma_padded(spec):
             # operands by TMA: blocked half activations, nine taps as shifted views of one haloed tile
             xb = inp.b
             if xb is None:
@@ -205,6 +215,12 @@ class UNet:
         _, ci, co, k, act = spec
         return k == 1 and not act and co <= 3 and ci % 4 == 0 and ci <= 64
 
+    def _tma_padded(self, spec):
+        """The network's input layer (fewer than 16 channels) on the TMA path, zero-padded to 16."""
+        name, ci, co, k, _ = spec
+        return (name == "enc1a" and k == 3 and ci < 16 and co % 8 == 0 and self.conv_path == "tma"
+                and self.gemm_backend == "tcgen05")
+
     def _blocked_ok(self, c):
         """Whether a c-channel activation may be handed over as blocked halves only."""
         return self.conv_path == "tma" and self.gemm_backend == "tcgen05" and c % 8 == 0
@@ -238,7 +254,12 @@ class UNet:
         else:
             K.smrt_nn_bias_act_bwd(da, z, act, dzf, self.grads[name + ".b"])
         dzh = None
-        if tma_w:
+        if tma_w and xshape[3] != ci:
+            # zero-padded input layer: the padded gradient, folded back onto the real channels
+            gp = t.zeros((co, 9 * xshape[3]), dtype=t.float32, device=self.device)
+            K.smrt_nn_conv3_wgrad_tma(xb, xshape, dzb, co, gp, 1.0, self._gemm_err)
+            K.smrt_nn_unpad3_add(gp, ci, xshape[3], gw)
+        elif tma_w:
             K.smrt_nn_conv3_wgrad_tma(xb, xshape, dzb, co, gw, 1.0, self._gemm_err)
         else:
             if col is None:         # the forward gathered from x; the weight gradient needs the matrix

@@ -30,6 +30,32 @@ def test_to_half_blocked_layout():
     assert np.array_equal(xb.cpu().numpy(), _blocked((0.5 * x).astype(np.float16)))
 
 
+def test_padding_kernels_for_a_narrow_input_layer():
+    """The 3-channel input as 16 zero-padded channels: blocked halves, padded weights, and the weight
+    gradient folded back -- element by element."""
+    import torch
+    r = _rng(21)
+    x = r.normal(size=(2, 5, 7, 3)).astype(np.float32)
+    xb = torch.empty(2 * 5 * 7 * 16, dtype=torch.float16, device="cuda")
+    S.smrt_nn_to_half_blocked_pad(torch.tensor(x, device="cuda"), 16, xb)
+    xp = np.zeros((2, 5, 7, 16), dtype=np.float32)
+    xp[..., :3] = x
+    w = r.normal(size=(8, 27)).astype(np.float32)
+    wh = torch.empty((8, 144), dtype=torch.float16, device="cuda")
+    S.smrt_nn_pad3(torch.tensor(w, device="cuda"), 3, 16, wh)
+    gp = torch.tensor(r.normal(size=(8, 144)).astype(np.float32), device="cuda")
+    gw0 = r.normal(size=(8, 27)).astype(np.float32)
+    gw = torch.tensor(gw0, device="cuda")
+    S.smrt_nn_unpad3_add(gp, 3, 16, gw)
+    torch.cuda.synchronize()
+    assert np.array_equal(xb.cpu().numpy(), _blocked(xp.astype(np.float16)))
+    whr = np.zeros((8, 9, 16), dtype=np.float16)
+    whr[:, :, :3] = w.reshape(8, 9, 3).astype(np.float16)
+    assert np.array_equal(wh.cpu().numpy(), whr.reshape(8, 144))
+    exp = gw0 + gp.cpu().numpy().reshape(8, 9, 16)[:, :, :3].reshape(8, 27)
+    assert np.array_equal(gw.cpu().numpy(), exp)
+
+
 @pytest.mark.parametrize("cout,C", [(5, 32), (48, 16), (130, 32)])
 def test_pack3_layout(cout, C):
     import torch
