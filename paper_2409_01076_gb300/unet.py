@@ -118,7 +118,8 @@ class UNet:
     def _half_weights(self):
         t = self.torch
         self._wh, self._wf, self._wp, self._wfp = {}, {}, {}, {}
-        for name, ci, co, k, _ in self.specs:
+        for spec in self.specs:
+            name, ci, co, k, _ = spec
             w = self.params[name + ".w"]
             h = t.empty(w.shape, dtype=t.float16, device=self.device)
             K.smrt_nn_to_half(w, h)
