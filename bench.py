@@ -391,6 +391,9 @@ def cpu_baseline(wl, budget_s=8.0):
                       % (side, side, wl["name"], steps, cores, sec, sec1)}
 
 
+METRIC = "D2Q9 SmrtLBM MLUPS + % HBM roofline"
+
+
 def reference_arm(args):
     rank, world, _ = dist_setup(args.gpus)
     if rank != 0:
@@ -412,12 +415,14 @@ def reference_arm(args):
         pool.terminate()
     mlups = cores * side * side * args.steps / sec / 1e6
     line = {
-        "impl": "reference", "metric": "D2Q9 SmrtLBM MLUPS", "value": round(mlups, 4), "unit": "MLUPS",
+        "impl": "reference", "metric": METRIC, "value": round(mlups, 4), "unit": "MLUPS",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(sec / args.steps * 1e3, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl["desc"], "sample": "%dx%d window per core per step" % (side, side),
-                   "l2": "CPU run; no GPU L2 involved"},
+        "config": {"workload": wl["desc"], "nodes": wl["nx"] * wl["ny"], "storage": "f64 populations (CPU oracle)",
+                   "layout": args.layout, "collision": args.kind, "l2": "CPU run; no GPU L2 involved",
+                   "parallelism": "one process per host core", "sample": "%dx%d window per core per step"
+                   % (side, side)},
         "cpu_baseline": {"value": round(mlups, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
                          "cpu": cpu_model(), "sample": "%dx%d window of %s per core, one update per step, FP64 C oracle in one "
                                    "process per host core" % (side, side, wl["name"])},
@@ -459,7 +464,7 @@ def gpu_arm(args):
     traffic_per_node, _ = committed_traffic(args.prec, args.layout, args.kind)
 
     result = {
-        "metric": "D2Q9 SmrtLBM MLUPS + % HBM roofline", "value": round(mlups, 1), "unit": "MLUPS",
+        "metric": METRIC, "value": round(mlups, 1), "unit": "MLUPS",
         "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
         "ms_per_step": round(ms / args.steps, 5), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if args.prec == "f32" else args.prec, "data": "synthetic",

@@ -58,6 +58,11 @@ def test_reference_arm_single_rank_json():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == cores
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["higher_is_better"] is True
+    # the same metric and workload as the GPU arm, so that the two lines compare
+    sys.path.insert(0, ROOT)
+    import bench
+    assert d["metric"] == bench.METRIC
+    assert d["config"]["workload"] == bench.workload("tgv8192", 0)["desc"]
 
 
 def test_reference_arm_under_torchrun_world2():
