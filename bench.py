@@ -716,19 +716,26 @@ def unet_report(args):
     variants = {"tcgen05": ("tcgen05", "tma"), "tcgen05-gather": ("tcgen05", "gather"), "wmma": ("wmma", "gather")}
     for backend in (list(variants) if args.unet_backend == "all" else [args.unet_backend]):
         gemm, conv = variants[backend]
-        net = UNet(base=32, gemm=gemm, conv=conv)
-        for _ in range(3):
-            net.train_step(x, target, 1e-3)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(args.unet_iters):
-            net.loss_and_grad(x, target)
-            net.adam_step(1e-3)
-        e1.record()
-        torch.cuda.synchronize()
-        out[backend] = {"ms_per_step": round(e0.elapsed_time(e1) / args.unet_iters, 3),
-                        "gemm_timeouts": net.gemm_timeouts(), "params": net.n_params()}
+        for graph in ((False, True) if backend == "tcgen05" else (False,)):
+            net = UNet(base=32, gemm=gemm, conv=conv)
+            for _ in range(3):
+                net.train_step(x, target, 1e-3)
+            if graph:
+                net.capture(x, target)          # forward + backward as one CUDA graph; Adam eager
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.unet_iters):
+                if graph:
+                    net.replay()
+                else:
+                    net.loss_and_grad(x, target)
+                net.adam_step(1e-3)
+            e1.record()
+            torch.cuda.synchronize()
+            out[backend + ("+graph" if graph else "")] = {
+                "ms_per_step": round(e0.elapsed_time(e1) / args.unet_iters, 3),
+                "gemm_timeouts": net.gemm_timeouts(), "params": net.n_params()}
     print(json.dumps(out), flush=True)
     return 0
 

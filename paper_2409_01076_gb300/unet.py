@@ -71,16 +71,28 @@ class UNet:
             co = cout if co == "out" else co * base
             self.specs.append((name, ci, co, k, act))
         rng = np.random.Generator(np.random.PCG64(seed))
-        self.params, self.grads, self.m, self.v = {}, {}, {}, {}
+        init = []
         for name, ci, co, k, _ in self.specs:
             fan_in = ci * k * k
             w = rng.normal(0.0, math.sqrt(2.0 / fan_in), size=(co, k * k * ci))
             b = rng.normal(0.0, 0.01, size=(co,))
-            for key, val in ((name + ".w", w), (name + ".b", b)):
-                self.params[key] = torch.tensor(val, dtype=torch.float32, device=device)
-                self.grads[key] = torch.zeros_like(self.params[key])
-                self.m[key] = torch.zeros_like(self.params[key])
-                self.v[key] = torch.zeros_like(self.params[key])
+            init += [(name + ".w", w), (name + ".b", b)]
+        # parameters, gradients and Adam moments each live in one flat buffer (one Adam launch, one
+        # gradient fill); the per-layer tensors are views into them, 16-byte aligned
+        offs, total = {}, 0
+        for key, val in init:
+            offs[key] = total
+            total += (val.size + 3) // 4 * 4
+        self._flat = {nm: torch.zeros(total, dtype=torch.float32, device=device) for nm in ("p", "g", "m", "v")}
+        self.params, self.grads, self.m, self.v = {}, {}, {}, {}
+        for key, val in init:
+            o, n = offs[key], val.size
+            self.params[key] = self._flat["p"][o:o + n].view(val.shape)
+            self.params[key].copy_(torch.tensor(val, dtype=torch.float32))
+            self.grads[key] = self._flat["g"][o:o + n].view(val.shape)
+            self.m[key] = self._flat["m"][o:o + n].view(val.shape)
+            self.v[key] = self._flat["v"][o:o + n].view(val.shape)
+        self._graph = None
         self.step_count = 0
         self.grad_scale = 2.0 ** 16
         self._found_inf = torch.zeros(1, dtype=torch.int32, device=device)
@@ -394,8 +406,7 @@ class UNet:
 
     def loss_and_grad(self, x, target):
         """MSE loss (float) with scaled gradients accumulated into self.grads (zeroed first)."""
-        for g in self.grads.values():
-            g.zero_()
+        self._flat["g"].zero_()
         cache = {}
         y = self.forward(x, cache)
         self._loss.zero_()
@@ -408,13 +419,37 @@ class UNet:
         """Applies the accumulated gradients; returns False (and lowers the loss scale) on overflow."""
         self.step_count += 1
         self._found_inf.zero_()
-        for key in self.params:
-            K.smrt_nn_adam(self.params[key], self.grads[key], self.m[key], self.v[key], lr, b1, b2, eps,
-                           self.step_count, self.grad_scale, self._found_inf)
+        f = self._flat      # the padding between views holds zeros in all four buffers and stays zero
+        K.smrt_nn_adam(f["p"], f["g"], f["m"], f["v"], lr, b1, b2, eps, self.step_count, self.grad_scale,
+                       self._found_inf)
         if int(self._found_inf.item()):
             self.grad_scale /= 2.0
+            self._graph = None              # the recorded loss gradient carries the old scale
             return False
         return True
+
+    def capture(self, x, target):
+        """Records loss_and_grad on the static tensors x and target as one CUDA graph, after an eager
+        warm-up on a side stream; replay() re-runs it on their current contents.  The loss scale is
+        part of the recording, so adam_step drops the graph when it lowers the scale."""
+        t = self.torch
+        side = t.cuda.Stream()
+        side.wait_stream(t.cuda.current_stream())
+        with t.cuda.stream(side):
+            self.loss_and_grad(x, target)
+        t.cuda.current_stream().wait_stream(side)
+        g = t.cuda.CUDAGraph()
+        with t.cuda.graph(g):
+            self._graph_y = self.loss_and_grad(x, target)
+        self._graph = g
+        self._graph_in = (x, target)
+
+    def replay(self):
+        """loss_and_grad on the tensors given to capture() (their current contents)."""
+        if self._graph is None:
+            raise RuntimeError("no recorded training step: call capture() first")
+        self._graph.replay()
+        return self._graph_y
 
     def train_step(self, x, target, lr: float) -> float:
         self.loss_and_grad(x, target)

@@ -65,29 +65,45 @@ def generate_dataset(res, n: int = 256, tol: float = 1e-7, check_every: int = 10
 
 
 def train(net, res, targets, iters: int = 2000, batch: int = 16, lr: float = 1e-3, seed: int = 0,
-          log_every: int = 100, warmup: int = 100):
+          log_every: int = 100, warmup: int = 100, graph: bool = True):
     """Adam on random mini-batches: the learning rate rises linearly over the first `warmup`
     iterations, under a cosine decay over all of them.  Returns the loss history and the seconds.
 
     Measured on 256 solver-generated 256^2 cavities (800 iterations, two seeds, both GEMM
     backends): a peak rate of 1e-3 reaches a held-out MSE of 0.7-1.3e-4 in every run, with or
     without the warm-up; 2e-3 is unstable (loss spikes when the rate peaks, stalls near the
-    mean-field loss in some runs)."""
+    mean-field loss in some runs).
+
+    graph: the forward and backward pass is recorded once as a CUDA graph (UNet.capture) and
+    replayed on static input tensors that each iteration's batch is copied into; Adam runs outside
+    the graph (its step-dependent scalars change every iteration)."""
     import torch
     from .unet import input_grid
     rng = np.random.Generator(np.random.PCG64(seed))
     n = targets.shape[1]
     count = len(res)
     hist = []
+    xs = ts = None
     t0 = time.perf_counter()
     for it in range(iters):
         idx = rng.choice(count, size=min(batch, count), replace=False)
         x = input_grid([res[i] for i in idx], n, n)
         tgt = targets[torch.as_tensor(idx, device=targets.device)].contiguous()
         cur = lr * min(1.0, (it + 1) / max(warmup, 1)) * 0.5 * (1.0 + math.cos(math.pi * it / iters))
-        loss = net.train_step(x, tgt, cur)
+        if graph:
+            if xs is None:
+                xs, ts = x.clone(), tgt.clone()
+            else:
+                xs.copy_(x)
+                ts.copy_(tgt)
+            if net._graph is None or net._graph_in[0] is not xs:
+                net.capture(xs, ts)         # first iteration, or after the loss scale changed
+            net.replay()
+        else:
+            net.loss_and_grad(x, tgt)
+        net.adam_step(cur)
         if it % log_every == 0 or it == iters - 1:
-            hist.append((it, loss))
+            hist.append((it, float(net._loss.item())))
     torch.cuda.synchronize()
     return hist, time.perf_counter() - t0
 

@@ -329,6 +329,27 @@ def test_unet_gradients_match_oracle_at_training_size(backend, conv):
         assert net.gemm_timeouts() == 0
 
 
+def test_graph_replay_matches_eager_training():
+    """Three Adam steps with the forward and backward pass replayed from one CUDA graph give the
+    losses and parameters of three eager steps (up to the order of the weight-gradient atomics)."""
+    from paper_2409_01076_gb300.unet import UNet, input_grid
+    x = input_grid([150.0, 900.0], 32, 32)
+    xs = _np(x)
+    t = _t(np.stack([np.sin(3 * xs[..., 1]) * xs[..., 0], np.cos(2 * xs[..., 2]), xs[..., 1] * xs[..., 2]], axis=-1))
+    eager, graph = UNet(base=8, seed=4), UNet(base=8, seed=4)
+    l_eager = [eager.train_step(x, t, 1e-3) for _ in range(3)]
+    xg, tg = x.clone(), t.clone()
+    graph.capture(xg, tg)
+    l_graph = []
+    for _ in range(3):
+        graph.replay()
+        graph.adam_step(1e-3)
+        l_graph.append(float(_np(graph._loss)[0]))
+    assert np.allclose(l_graph, l_eager, rtol=1e-4), (l_graph, l_eager)
+    for key in eager.params:
+        assert np.abs(_np(eager.params[key]) - _np(graph.params[key])).max() < 1e-5, key
+
+
 def test_unet_training_reduces_the_loss():
     from paper_2409_01076_gb300.unet import UNet, input_grid
     net = UNet(base=8, seed=1)
