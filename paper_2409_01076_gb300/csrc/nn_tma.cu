@@ -432,6 +432,98 @@ conv3_wgrad_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constan
     teardown<kCols>(tmem);
 }
 
+// ---- weight gradient of narrow layers (C = 16 or 32): taps grouped along M --------------------
+// With C < 128 most of the 128 MMA rows of conv3_wgrad_kernel would be padding.  Here each tile
+// loads its nine tap-shifted 16 x 8 windows (box {64, 16, C/8, 1} at (x0 + kx - 1, y0 + ky - 1)) into
+// nine consecutive slots of (C/8) x 2,048 B, so T = 128 / C consecutive taps form one MN-major operand
+// of 128 rows = (tap, channel): start = slot(g T) + 2j x 128 B, leading byte offset 128 B (next image
+// row), stride byte offset 2,048 B (next 8 channels, continuing into the next tap's slot).  ceil(9 / T)
+// groups of eight K = 16 MMAs per tile instead of nine; the rows of a last group's missing taps read
+// whatever follows the ninth slot and are never stored.
+template <int C>
+__global__ void __launch_bounds__(128)
+conv3_wgrad_grouped_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmz, int H,
+                           int W, int cout, int tiles_x, int tiles_y, int ntiles, int nbk, int per, int nstages,
+                           int stage_bytes, float alpha, float *gw, int ldg, int *err)
+{
+    constexpr int T = 128 / C, NG = (9 + T - 1) / T, SLOT = (C / 8) * kDzPlane;
+    constexpr uint32_t kCols = NG * kWgTN <= 64 ? 64 : 128;
+    static_assert(NG * kWgTN <= 128 && 128 % C == 0, "narrow channel counts only");
+    extern __shared__ unsigned char dyn_raw[];
+    __shared__ __align__(8) unsigned long long full[kWgStages], empty[kWgStages], done;
+    __shared__ uint32_t tmem_holder;
+    __shared__ int failed;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nb = blockIdx.x % nbk;
+    const int t_beg = blockIdx.y * per;
+    const int t_end = min(ntiles, t_beg + per);
+    if (t_beg >= t_end) return;             // uniform over the CTA
+    constexpr uint32_t kTx = 9 * SLOT + 4 * kDzPlane;
+    const uint32_t base = (smem_u32(dyn_raw) + 1023u) & ~1023u;
+    const uint32_t tmem = setup<kCols>(&tmem_holder, full, empty, &done, nstages, &failed);
+    const int n_it = t_end - t_beg;
+
+    if (warp == 0 && lane == 0) {
+        asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&tmx)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&tmz)) : "memory");
+        for (int it = 0; it < n_it; ++it) {
+            const int s = it % nstages;
+            if (it >= nstages && !wait_or_fail(smem_u32(&empty[s]), (uint32_t)((it / nstages - 1) & 1), &failed, err))
+                break;
+            const int t = t_beg + it, per_img = tiles_x * tiles_y;
+            const int img = t / per_img, rem = t - img * per_img;
+            const int x0 = (rem % tiles_x) * kTilePx, y0 = (rem / tiles_x) * kTileRows;
+            const uint32_t st = base + (uint32_t)(s * stage_bytes), fb = smem_u32(&full[s]);
+            expect_tx(fb, kTx);
+            #pragma unroll 1
+            for (int tap = 0; tap < 9; ++tap)
+                tma_load_4d(st + (uint32_t)(tap * SLOT), &tmx, 8 * (x0 + tap % 3 - 1), y0 + tap / 3 - 1, 0, img, fb);
+            tma_load_4d(st + 9u * SLOT, &tmz, 8 * x0, y0, 4 * nb, img, fb);
+        }
+    } else if (warp == 1 && lane == 0) {
+        for (int it = 0; it < n_it; ++it) {
+            const int s = it % nstages;
+            if (!wait_or_fail(smem_u32(&full[s]), (uint32_t)((it / nstages) & 1), &failed, err)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t st = base + (uint32_t)(s * stage_bytes);
+            #pragma unroll
+            for (int g = 0; g < NG; ++g) {
+                #pragma unroll
+                for (int j = 0; j < kTileRows / 2; ++j)        // K = 16 pixels: image rows 2j, 2j + 1
+                    mma_f16(tmem + (uint32_t)(g * kWgTN),
+                            desc(st + (uint32_t)(g * T * SLOT + 2 * j * 128), 128, kDzPlane),
+                            desc(st + 9u * SLOT + (uint32_t)(2 * j * 128), 128, kDzPlane),
+                            idesc<kWgTN, true>(), (it > 0 || j > 0) ? 1u : 0u);
+            }
+            commit(smem_u32(&empty[s]));
+        }
+        commit(smem_u32(&done));
+    }
+    __syncwarp();
+    wait_or_fail(smem_u32(&done), 0u, &failed, err);
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+
+    if (!failed) {
+        const int m = warp * 32 + lane, u = m / C, c = m % C;
+        #pragma unroll 1
+        for (int g = 0; g < NG; ++g) {
+            uint32_t r[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(g * kWgTN), r);
+            const int tap = g * T + u;
+            if (tap >= 9) continue;
+            float *gp = gw + (size_t)tap * C + c;
+            #pragma unroll
+            for (int j = 0; j < kWgTN; ++j) {
+                const int o = kWgTN * nb + j;
+                if (o < cout) atomicAdd(gp + (size_t)o * ldg, alpha * __uint_as_float(r[j]));
+            }
+        }
+    }
+    teardown<kCols>(tmem);
+}
+
 // ---- layout kernels ------------------------------------------------------------------------
 // xb[((n * C/8 + g) * H + y) * W + x][e] = half(scale * x[n][y][x][8 g + e]); one thread per 8 channels.
 __global__ void to_half_blocked_kernel(const float *__restrict__ x, int N, int H, int W, int C, float scale,
@@ -730,6 +822,59 @@ extern "C" int smrt_nn_conv3_tma_bias_act(const void *xb, int N, int H, int W, i
     return SMRT_OK;
 }
 
+// Launch of conv3_wgrad_grouped_kernel<C> (C = 16 or 32): one CTA per SM over splits of the pixel tiles.
+int wgrad_grouped(const void *xb, int N, int H, int W, int C, const void *dzb, int cout, float alpha, float *gw, int ldg,
+                  int *err, void *stream, const CUtensorMap &tmz)
+{
+    const int tiles_x = (W + kTilePx - 1) / kTilePx, tiles_y = (H + kTileRows - 1) / kTileRows;
+    const long long ntiles = (long long)N * tiles_x * tiles_y;
+    CUtensorMap tmx;
+    const CUresult r = blocked_map(&tmx, xb, N, H, W, C, kTilePx, kTileRows, C / 8);
+    if (r != CUDA_SUCCESS)
+        return tma_fail(SMRT_ERR_CUDA, "smrt_nn_conv3_wgrad_tma: tensor map rejected (%d)", (int)r);
+    const int nbk = (cout + kWgTN - 1) / kWgTN;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 148;
+    long long splits = sms / nbk;
+    if (splits < 1) splits = 1;
+    if (splits > ntiles) splits = ntiles;
+    const int per = (int)((ntiles + splits - 1) / splits);
+    splits = (ntiles + per - 1) / per;
+    const int slot = (C / 8) * kDzPlane, T = 128 / C, ng = (9 + T - 1) / T;
+    const int stage = (9 * slot + 4 * kDzPlane + 1023) / 1024 * 1024;
+    const int reach = ng * T * slot;                 // a stage's last group reads this far
+    int nstages = kWgStages;
+    auto need = [&](int n) { return (size_t)(n - 1) * stage + (size_t)(stage > reach ? stage : reach); };
+    while (nstages > 1 && need(nstages) + 1024 > 220 * 1024) --nstages;
+    const size_t smem = need(nstages) + 1024;
+    if (smem > 220 * 1024 || nbk > 65535 || splits > 65535)
+        return tma_fail(SMRT_ERR_ARG, "smrt_nn_conv3_wgrad_tma: sizes out of range (C %d cout %d)", C, cout);
+    cudaStream_t s = (cudaStream_t)stream;
+    dim3 grid(nbk, (unsigned)splits);
+    cudaError_t e;
+    if (C == 16) {
+        static bool attr16 = false;
+        e = attr16 ? cudaSuccess : cudaFuncSetAttribute(conv3_wgrad_grouped_kernel<16>,
+                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        attr16 = attr16 || e == cudaSuccess;
+        if (e == cudaSuccess)
+            conv3_wgrad_grouped_kernel<16><<<grid, 128, smem, s>>>(tmx, tmz, H, W, cout, tiles_x, tiles_y, (int)ntiles,
+                                                                   nbk, per, nstages, stage, alpha, gw, ldg, err);
+    } else {
+        static bool attr32 = false;
+        e = attr32 ? cudaSuccess : cudaFuncSetAttribute(conv3_wgrad_grouped_kernel<32>,
+                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        attr32 = attr32 || e == cudaSuccess;
+        if (e == cudaSuccess)
+            conv3_wgrad_grouped_kernel<32><<<grid, 128, smem, s>>>(tmx, tmz, H, W, cout, tiles_x, tiles_y, (int)ntiles,
+                                                                   nbk, per, nstages, stage, alpha, gw, ldg, err);
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return tma_fail(SMRT_ERR_CUDA, "smrt_nn_conv3_wgrad_tma: %s", cudaGetErrorString(e));
+    return SMRT_OK;
+}
+
 extern "C" int smrt_nn_conv3_wgrad_tma(const void *xb, int N, int H, int W, int C, const void *dzb, int cout,
                                        float alpha, float *gw, int ldg, int *err, void *stream)
 {
@@ -747,6 +892,7 @@ extern "C" int smrt_nn_conv3_wgrad_tma(const void *xb, int N, int H, int W, int 
     if (r != CUDA_SUCCESS)
         return tma_fail(SMRT_ERR_CUDA, "smrt_nn_conv3_wgrad_tma: tensor map rejected (%d)", (int)r);
 
+    if (C == 16 || C == 32) return wgrad_grouped(xb, N, H, W, C, dzb, cout, alpha, gw, ldg, err, stream, tmz);
     const int mbk = (C + 8 * kWgPlanes - 1) / (8 * kWgPlanes), nbk = (cout + kWgTN - 1) / kWgTN;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
