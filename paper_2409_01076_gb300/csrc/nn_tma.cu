@@ -2,10 +2,14 @@
 // (cp.async.bulk.tensor / cp.async.bulk), where the nine taps of the filter are nine shifted views
 // of ONE haloed input tile in shared memory: no im2col matrix or tile is ever written.
 //
-//   smrt_nn_to_half_blocked  float32 NHWC -> half, channel-group-blocked [N][C/8][H][W][8]
-//   smrt_nn_pack3            3x3 weights -> [n-block][16-channel chunk][9 taps x 2 groups][TN][8]
-//   smrt_nn_conv3_tma        y = conv3x3(x, w)            (forward; input gradient with flipped w)
-//   smrt_nn_conv3_wgrad_tma  dW += sum_pixels x(shifted) dz  (weight gradient)
+//   smrt_nn_to_half_blocked     float32 NHWC -> half, channel-group-blocked [N][C/8][H][W][8]
+//   smrt_nn_to_half_blocked_pad the same, zero-padded to more channels (a narrow input layer)
+//   smrt_nn_pack3               3x3 weights -> [n-block][16-channel chunk][9 taps x 2 groups][TN][8]
+//   smrt_nn_pad3 / _unpad3_add  3x3 weights zero-padded to more input channels / gradient folded back
+//   smrt_nn_conv3_tma           y = conv3x3(x, w)  (forward; input gradient with flipped w)
+//   smrt_nn_conv3_tma_bias_act  the same with bias + SiLU in the epilogue (z, a, blocked a)
+//   smrt_nn_conv3_wgrad_tma     dW += sum_pixels x(shifted) dz  (weight gradient; for 16 or 32 input
+//                               channels the taps are grouped along the MMA rows)
 //
 // Blocked activations.  In [N][C/8][H][W][8] one image row of one 8-channel group is W * 16
 // contiguous bytes, so a TMA box over the 4-D view (8W halves, H, C/8, N) brings 18 halo rows of
