@@ -680,7 +680,9 @@ cudaError_t launch_conv3_tma(const CUtensorMap &tmx, const __half *wp, int N, in
 {
     const int ntn = (cout + TN - 1) / TN;
     const int nchunks = C / kChunk;
-    const int nstages = nchunks < kFwdStages ? nchunks : kFwdStages;
+    // a 32-wide tile with at most two chunks: one stage (15 KB), so that 14 CTAs share an SM and
+    // hide each other's copy latency; otherwise up to four stages per CTA
+    const int nstages = (TN == 32 && nchunks <= 2) ? 1 : (nchunks < kFwdStages ? nchunks : kFwdStages);
     // shared memory also caps the CTAs per SM so that their accumulators fit in the 512 TMEM
     // columns: with 128 columns each, at most 4 CTAs may be resident, so reserve >= 2 stages
     const int reserve = (TN == 128 && nstages < 2) ? 2 : nstages;
