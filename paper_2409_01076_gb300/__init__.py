@@ -64,11 +64,12 @@ def _ptr(a, shape, name, writable):
 
 
 class Handle:
-    """An smrt_t* with its lattice size; destroyed when garbage-collected."""
+    """An smrt_t* with its lattice size, lid speed and boundary flags; destroyed when garbage-collected."""
 
-    def __init__(self, ptr: int, nx: int, ny: int):
+    def __init__(self, ptr: int, nx: int, ny: int, u_lid: float = 0.0, bc: int = 0):
         self.ptr = ctypes.c_void_p(ptr)
         self.nx, self.ny = nx, ny
+        self.u_lid, self.bc = float(u_lid), int(bc)
 
     def __del__(self):
         try:
@@ -86,7 +87,7 @@ def smrt_create(nx: int, ny: int, tau: float, u_lid: float = 0.0, bc: int = CAVI
     rc = _lib.load().smrt_create(nx, ny, tau, u_lid, bc, ctypes.byref(out))
     if rc != SMRT_OK:
         raise SmrtError(rc, smrt_last_error(None))
-    return Handle(out.value, nx, ny)
+    return Handle(out.value, nx, ny, u_lid, bc)
 
 
 def smrt_set_option(h: Handle, key: int, value: float) -> None:
@@ -315,3 +316,6 @@ from .nn import (smrt_nn_adam, smrt_nn_add, smrt_nn_avgpool2, smrt_nn_avgpool2_b
                  smrt_nn_conv1x1_small, smrt_nn_conv1x1_small_bwd,
                  smrt_nn_im2col3, smrt_nn_mse, smrt_nn_resize_bilinear, smrt_nn_to_half, smrt_nn_to_half_rows,
                  smrt_nn_upsample2, smrt_nn_upsample2_bwd)
+
+# ---- checkpoint files of a single lattice ------------------------------------------------
+from .checkpoint import load_checkpoint, read_checkpoint, save_checkpoint, write_checkpoint  # noqa: E402,F401

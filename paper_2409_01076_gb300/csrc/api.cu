@@ -405,6 +405,7 @@ int smrt_sync(smrt_t *h)
 
 int smrt_step(smrt_t *h, long long n)
 {
+    smrt::TraceRange trace("smrt_step");
     if (!h) return SMRT_ERR_ARG;
     if (n < 0) return fail(h, SMRT_ERR_ARG, "smrt_step: n must be >= 0 (got %lld)", n);
     int rc = begin(h);
@@ -430,6 +431,7 @@ int smrt_step(smrt_t *h, long long n)
 
 int smrt_macros(smrt_t *h, double *rho, double *u)
 {
+    smrt::TraceRange trace("smrt_macros");
     int rc = begin(h);
     if (rc != SMRT_OK) return rc;
     if (!rho && !u) return SMRT_OK;
@@ -469,6 +471,7 @@ int smrt_macros(smrt_t *h, double *rho, double *u)
 
 int smrt_residual(smrt_t *h, double *r, double *sums)
 {
+    smrt::TraceRange trace("smrt_residual");
     int rc = begin(h);
     if (rc != SMRT_OK) return rc;
     DeviceGuard g(h->device);

@@ -711,6 +711,7 @@ int smrt_batch_set_shape(smrt_batch_t *b, int shape)
 
 int smrt_batch_step(smrt_batch_t *b, long long n)
 {
+    smrt::TraceRange trace("smrt_batch_step");
     if (!b) return SMRT_ERR_ARG;
     if (n < 0) return bfail(b, SMRT_ERR_ARG, "smrt_batch_step: n must be >= 0");
     if (b->list_dirty) {
@@ -803,6 +804,7 @@ int smrt_batch_autotune(smrt_batch_t *b, int steps, int *choice)
 int smrt_batch_run(smrt_batch_t *b, double tol, long long check_every, long long max_steps, int residual_kind,
                    int *n_active)
 {
+    smrt::TraceRange trace("smrt_batch_run");
     if (!b) return SMRT_ERR_ARG;
     if (!(tol > 0.0) || check_every < 1 || max_steps < 0)
         return bfail(b, SMRT_ERR_ARG, "smrt_batch_run: need tol > 0, check_every >= 1, max_steps >= 0");

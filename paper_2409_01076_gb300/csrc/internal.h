@@ -4,11 +4,21 @@
 
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stddef.h>
 
 #include "smrt.h"
 
 namespace smrt {
+
+// An NVTX range over one entry point (visible in Nsight timelines; header-only NVTX 3, which does
+// nothing unless a profiling tool is attached).
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 
 // How the stored arrays map to the canonical f(t): the two-buffer layout, or the
 // in-place layout before an even / odd step (t even / t odd).

@@ -313,6 +313,30 @@ def test_checkpoint_resume(prec, layout):
     S.smrt_destroy(h2)
 
 
+@pytest.mark.parametrize("prec,layout", [("f32", "ab"), ("f32", "aa"), ("f16", "aa"), ("f64", "ab")])
+def test_checkpoint_file_resume(prec, layout, tmp_path):
+    """save_checkpoint at an odd t, load_checkpoint into a new handle, continue: the same as running
+    straight through (bit for bit below FP64 storage), with lattice, options and t restored."""
+    h1 = make(48, 30, 0.61, 0.08, W.COUETTE, prec=prec, layout=layout, kind="two_tau", tau_s=0.8)
+    S.smrt_step(h1, 37)
+    path = str(tmp_path / "state.ckp")
+    S.save_checkpoint(h1, path)
+    S.smrt_step(h1, 20)
+    straight = get_f(h1)
+    h2 = S.load_checkpoint(path)
+    assert S.smrt_time(h2) == 37 and (h2.nx, h2.ny) == (48, 30)
+    for key in (S.SMRT_OPT_PRECISION, S.SMRT_OPT_LAYOUT, S.SMRT_OPT_COLLISION, S.SMRT_OPT_TAU, S.SMRT_OPT_TAU_S):
+        assert S.smrt_get_option(h2, key) == S.smrt_get_option(h1, key), key
+    S.smrt_step(h2, 20)
+    resumed = get_f(h2)
+    if prec == "f64":
+        assert rel_f(resumed, straight) <= 1e-15
+    else:
+        assert np.array_equal(resumed, straight)
+    S.smrt_destroy(h1)
+    S.smrt_destroy(h2)
+
+
 def test_stream_binding_and_device_macros():
     import torch
     s = torch.cuda.Stream()
