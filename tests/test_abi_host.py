@@ -91,3 +91,36 @@ def test_null_handle_is_rejected():
     out = ctypes.c_void_p(1)
     assert lib.smrt_create(0, 0, 0.7, 0.0, 0, ctypes.byref(out)) == S.SMRT_ERR_ARG
     assert out.value is None
+
+
+# The TMA-convolution and fused element-wise entry points check their arguments before any CUDA
+# call: each of these is rejected with SMRT_ERR_ARG and a message naming the function (no GPU needed).
+_BAD_NN_CALLS = [
+    ("smrt_nn_conv3_tma", (None, 1, 4, 4, 24, None, 8, 1.0, 0.0, None, 8, None, None)),
+    ("smrt_nn_conv3_tma_bias_act", (None, 1, 4, 4, 16, None, 12, None, 1, None, None, None, None, None)),
+    ("smrt_nn_conv3_wgrad_tma", (None, 1, 4, 4, 16, None, 12, 1.0, None, 144, None, None)),
+    ("smrt_nn_pack3", (None, 8, 24, None, None)),
+    ("smrt_nn_to_half_blocked", (None, 1, 4, 4, 12, 1.0, None, None)),
+    ("smrt_nn_to_half_blocked_pad", (None, 1, 4, 4, 3, 12, 1.0, None, None)),
+    ("smrt_nn_pad3", (None, 8, 3, 2, None, None)),
+    ("smrt_nn_unpad3_add", (None, 8, 3, 16, None, None)),
+    ("smrt_nn_bias_act_blocked", (None, None, 1, 4, 4, 12, 1, None, None, None, None)),
+    ("smrt_nn_bias_act_bwd_blocked", (None, None, 1, 4, 4, 12, 1, None, None, None, None)),
+    ("smrt_nn_avgpool2_blocked", (None, 1, 3, 4, 8, None, None, None)),
+    ("smrt_nn_upcat", (None, 1, 2, 2, 12, None, 8, None, None, None)),
+    ("smrt_nn_upcat_bwd", (None, 1, 2, 2, 6, 4, None, None, None)),
+    ("smrt_nn_conv1x1_small", (None, 16, 32, None, None, 4, None, None)),
+    ("smrt_nn_conv1x1_small_bwd", (None, None, 16, 32, None, 3, None, None, None, None)),
+]
+
+
+@pytest.mark.parametrize("name,args", _BAD_NN_CALLS, ids=[c[0] for c in _BAD_NN_CALLS])
+def test_nn_entry_points_reject_bad_arguments_on_the_host(name, args):
+    rc = getattr(_lib.load(), name)(*args)
+    assert rc == S.SMRT_ERR_ARG, (name, rc)
+    assert name in S.smrt_last_error(None)
+
+
+def test_pack3_halves_rejects_narrow_chunks():
+    assert S.smrt_nn_pack3_halves(8, 24) == -1 and S.smrt_nn_pack3_halves(0, 32) == -1
+    assert S.smrt_nn_pack3_halves(130, 32) == 9 * 32 * 256
