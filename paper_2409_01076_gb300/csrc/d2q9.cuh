@@ -51,24 +51,28 @@ template <int PREC> struct Prec;
 template <> struct Prec<SMRT_PREC_F64> {
     using R = double;
     using C = double;
+    static constexpr bool kExactWeights = true;
     static __device__ __forceinline__ C to_c(R r) { return r; }
     static __device__ __forceinline__ R to_r(C c) { return c; }
 };
 template <> struct Prec<SMRT_PREC_F32> {
     using R = float;
     using C = float;
+    static constexpr bool kExactWeights = true;
     static __device__ __forceinline__ C to_c(R r) { return r; }
     static __device__ __forceinline__ R to_r(C c) { return c; }
 };
 template <> struct Prec<SMRT_PREC_F16> {
     using R = unsigned short;
     using C = float;
+    static constexpr bool kExactWeights = false;
     static __device__ __forceinline__ C to_c(R r) { return __half2float(__ushort_as_half(r)); }
     static __device__ __forceinline__ R to_r(C c) { return __half_as_ushort(__float2half_rn(c)); }
 };
 template <> struct Prec<SMRT_PREC_BF16> {
     using R = unsigned short;
     using C = float;
+    static constexpr bool kExactWeights = false;
     static __device__ __forceinline__ C to_c(R r) { return __bfloat162float(__ushort_as_bfloat16(r)); }
     static __device__ __forceinline__ R to_r(C c) { return __bfloat16_as_ushort(__float2bfloat16_rn(c)); }
 };
@@ -204,13 +208,42 @@ __device__ __forceinline__ size_t at(long long plane_elems, int pitch, int plane
 }
 
 // ---- collision ------------------------------------------------------------------
+// x * w for the D2Q9 weight w (4/9, 1/9 or 1/36), with the product rounded as if the
+// weight were exact.  In float, w rounds to fl(w) = w (1 + 7.45e-9) for all three
+// weights; a plain product would scale the equilibrium's mass and momentum by that
+// factor at every collision (sum_a w_a = 1 and sum_a w_a e_a e_a = 1/3 hold for
+// fl(w) only up to it).  The update then pushes the flow along itself by 7.45e-9 of
+// its momentum per step, a coherent bias that grows linearly in time.  The split
+// w = hi + lo (hi = fl(w), lo = fl(w - hi)) and one fused multiply-add remove it.
+// Doubles keep the plain product: there the same bias is about 1e-17 per step.  So do the 16-bit
+// storage formats (EXACT = false): rounding a stored offset to 11 or 8 significant bits moves it by
+// 1e-4 to 1e-3 of itself each step, which buries the 7e-9, while the two extra operations per
+// population cost their near-ALU-bound kernels several per cent.
+template <class C, bool EXACT = true>
+struct WeightMul {
+    template <int A>
+    static __device__ __forceinline__ C mul(C x) { return wgt<C>(A) * x; }
+};
+template <>
+struct WeightMul<float, true> {
+    template <int A>
+    static __device__ __forceinline__ float mul(float x)
+    {
+        constexpr double w = wgt<double>(A);
+        constexpr float hi = (float)w;
+        constexpr float lo = (float)(w - (double)hi);
+        return fmaf(hi, x, lo * x);
+    }
+};
+
 // In:  g[a] = f_a - w_a (canonical offsets at one node).
 // Out: g[a] = f*_a - w_a (post-collision offsets).
 // Returns false when rho is not a positive finite number (divergence).
 //
 // Moments (Eq. fea-0):   rho = 1 + sum g,  j = sum e_a g_a,  u = j / rho.
-// Equilibrium offsets (Eq. feq-full):
-//   f^eq_a - w_a = w_a [ (rho - 1) + rho (3 e.u + 9/2 (e.u)^2 - 3/2 u.u) ].
+// Equilibrium offsets (Eq. feq-full), written with rho u = j so that the momentum of
+// the equilibrium is j itself rather than rho (j / rho) rounded twice:
+//   f^eq_a - w_a = w_a [ (rho - 1) + 3 e.j + 9/2 (e.j)(e.u) - 3/2 j.u ].
 // SmrtLBM (Eq. SmrtLBM-1): with n_k = f_k - f^eq_k the indicator sum is
 //   C1 = (-n1 + n2 - n3 + n4)/4 for a in 1..4 and C2 = (-n5 + n6 - n7 + n8)/4 for
 //   a in 5..8, so with Pxx = n1 - n2 + n3 - n4 = -4 C1 and Pxy = n5 - n6 + n7 - n8 = -4 C2
@@ -218,9 +251,10 @@ __device__ __forceinline__ size_t at(long long plane_elems, int pitch, int plane
 //   s = (+,-,+,-) over a = 1..4 (P = Pxx) and over a = 5..8 (P = Pxy), f*_0 = f^eq_0.
 // SRT (Eq. lb.srt): f*_a = f_a - (f_a - f^eq_a) / tau.
 // Two-tau (Eq. SmrtLBM-lb.1.5): f*_a = f_a - (f_a - f^eq_a)/tau_s + s_a (1/tau_s - 1/tau)/4 P.
-template <int KIND, class C>
+template <int KIND, bool EXACT = true, class C>
 __device__ __forceinline__ bool collide(const Params<C> &p, C g[9])
 {
+    using M = WeightMul<C, EXACT>;
     const C drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
     const C rho = C(1) + drho;
     const C jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
@@ -229,24 +263,23 @@ __device__ __forceinline__ bool collide(const Params<C> &p, C g[9])
     const C ux = jx * inv, uy = jy * inv;
     const bool ok = (rho > C(0)) && (rho < C(INFINITY));
 
-    const C base = drho - C(1.5) * rho * (ux * ux + uy * uy);
-    const C r45 = C(4.5) * rho, r3 = C(3) * rho;
-    const C sp = ux + uy, sm = ux - uy;
-    const C axx = base + r45 * ux * ux, bxx = r3 * ux;
-    const C ayy = base + r45 * uy * uy, byy = r3 * uy;
-    const C app = base + r45 * sp * sp, bpp = r3 * sp;
-    const C amm = base + r45 * sm * sm, bmm = r3 * sm;
-    const C W0 = wgt<C>(0), W1 = wgt<C>(1), W5 = wgt<C>(5);
+    const C base = drho - C(1.5) * (jx * ux + jy * uy);
+    const C jp = jx + jy, jm = jx - jy;
+    const C up = ux + uy, um = ux - uy;
+    const C axx = base + C(4.5) * jx * ux, bxx = C(3) * jx;
+    const C ayy = base + C(4.5) * jy * uy, byy = C(3) * jy;
+    const C app = base + C(4.5) * jp * up, bpp = C(3) * jp;
+    const C amm = base + C(4.5) * jm * um, bmm = C(3) * jm;
     C q[9];
-    q[0] = W0 * base;
-    q[1] = W1 * (axx + bxx);
-    q[3] = W1 * (axx - bxx);
-    q[2] = W1 * (ayy + byy);
-    q[4] = W1 * (ayy - byy);
-    q[5] = W5 * (app + bpp);
-    q[7] = W5 * (app - bpp);
-    q[8] = W5 * (amm + bmm);
-    q[6] = W5 * (amm - bmm);
+    q[0] = M::template mul<0>(base);
+    q[1] = M::template mul<1>(axx + bxx);
+    q[3] = M::template mul<3>(axx - bxx);
+    q[2] = M::template mul<2>(ayy + byy);
+    q[4] = M::template mul<4>(ayy - byy);
+    q[5] = M::template mul<5>(app + bpp);
+    q[7] = M::template mul<7>(app - bpp);
+    q[8] = M::template mul<8>(amm + bmm);
+    q[6] = M::template mul<6>(amm - bmm);
 
     if (KIND == SMRT_COLLISION_SRT) {
         #pragma unroll
