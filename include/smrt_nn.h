@@ -110,6 +110,22 @@ SMRT_API int smrt_nn_pack3(const void *w, int cout, int C, void *wp, void *strea
 SMRT_API int smrt_nn_conv3_tma(const void *xb, int N, int H, int W, int C, const void *wp, int cout, float alpha,
                                float beta, float *y, int ldy, int *err, void *stream);
 
+/* Reads the error word that the tensor-core kernels above set when a bounded wait gives up:
+ * waits for `stream`, reads *err (device int) and returns SMRT_OK if it is 0.  Otherwise it
+ * resets *err to 0 and returns SMRT_ERR_TIMEOUT: the blocks that gave up skipped their
+ * epilogues (their tensor memory was still released), so every output written since the
+ * previous check is suspect.  Synchronises the stream. */
+SMRT_API int smrt_nn_check(int *err, void *stream);
+
+/* Test hook for the failure path of smrt_nn_conv3_tma (not for computing anything): the same
+ * launch, with alpha = 1 and beta = 0, but the TMA producer of every block issues nothing and
+ * each wait gives up after wait_ms milliseconds (1e-3 <= wait_ms <= 1000) instead of one second.
+ * Every block therefore times out with no copy and no MMA in flight, sets *err = 1 (err is
+ * required), leaves y untouched and releases its tensor memory; smrt_nn_check then returns
+ * SMRT_ERR_TIMEOUT and the next ordinary call runs normally.  The paper has no counterpart. */
+SMRT_API int smrt_nn_conv3_tma_wait_test(const void *xb, int N, int H, int W, int C, const void *wp, int cout,
+                                         float *y, int ldy, int *err, double wait_ms, void *stream);
+
 /* smrt_nn_conv3_tma with the bias and the activation in its epilogue (the float32 convolution output
  * never goes to memory): v = conv + bias[o], z = v, a = SiLU(v) (act) or v, ab = half(a) blocked,
  * each written when its pointer is not NULL (z, a: N*H*W rows of cout float32; ab: the blocked layout

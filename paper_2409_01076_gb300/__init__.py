@@ -138,11 +138,20 @@ def smrt_residual_noalloc(f, tau: float, u_lid: float = 0.0, bc: int = CAVITY,
     f is a CUDA float64 tensor (9, ny, nx) holding f(t).  `out` may be a CUDA
     float64 tensor of 4 elements (the call then only enqueues work) or None, in
     which case the call waits and returns (r, (sum rho, sum rho ux, sum rho uy)).
+    stream: a torch.cuda.Stream or raw cudaStream_t; None means torch's current
+    stream, the one on which the caller's f was most likely written.
     """
     import numpy as np
+    import torch
+    if not (isinstance(f, torch.Tensor) and f.is_cuda):
+        raise TypeError("f must be a CUDA float64 tensor of shape (9, ny, nx)")
+    if out is not None and not (isinstance(out, torch.Tensor) and out.is_cuda):
+        raise TypeError("out must be a CUDA float64 tensor of 4 elements (or None for a host result)")
     _, ny, nx = tuple(f.shape)
     fp = _ptr(f, (9, ny, nx), "f", False)
-    raw = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
+    if stream is None:
+        stream = torch.cuda.current_stream(f.device)
+    raw = int(getattr(stream, "cuda_stream", stream))
     host = out is None
     res = np.empty(4) if host else out
     rc = _lib.load().smrt_residual_noalloc(fp, nx, ny, tau, u_lid, bc, collision, tau_s,
@@ -310,6 +319,7 @@ def smrt_batch_destroy(b: BatchHandle) -> None:
 from .nn import (smrt_nn_adam, smrt_nn_add, smrt_nn_avgpool2, smrt_nn_avgpool2_bwd, smrt_nn_bias_act,  # noqa: E402
                  smrt_nn_bias_act_bwd, smrt_nn_col2im3, smrt_nn_concat, smrt_nn_concat_bwd, smrt_nn_flip3, smrt_nn_gemm,
                  smrt_nn_gemm_tc, smrt_nn_conv3_tc, smrt_nn_conv3_tma, smrt_nn_conv3_wgrad_tma, smrt_nn_conv3_tma_bias_act,
+                 smrt_nn_check, smrt_nn_conv3_tma_wait_test,
                  smrt_nn_pack3, smrt_nn_pack3_halves, smrt_nn_to_half_blocked, smrt_nn_bias_act_blocked,
                  smrt_nn_to_half_blocked_pad, smrt_nn_pad3, smrt_nn_unpad3_add,
                  smrt_nn_bias_act_bwd_blocked, smrt_nn_avgpool2_blocked, smrt_nn_upcat, smrt_nn_upcat_bwd,

@@ -113,8 +113,8 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// Waits for the phase of parity `parity` of mbarrier `mb`; false after kWaitNs without it.
-__device__ __forceinline__ bool wait_parity(uint32_t mb, uint32_t parity)
+// Waits for the phase of parity `parity` of mbarrier `mb`; false after limit_ns without it.
+__device__ __forceinline__ bool wait_parity(uint32_t mb, uint32_t parity, unsigned long long limit_ns)
 {
     const unsigned long long t0 = global_ns();
     for (;;) {
@@ -123,17 +123,18 @@ __device__ __forceinline__ bool wait_parity(uint32_t mb, uint32_t parity)
                      "selp.u32 %0, 1, 0, p;\n\t}"
                      : "=r"(done) : "r"(mb), "r"(parity) : "memory");
         if (done) return true;
-        if (global_ns() - t0 > kWaitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
 }
 
 // A bounded wait that records a failure and then waits once more (also bounded).
-__device__ __forceinline__ bool wait_or_fail(uint32_t mb, uint32_t parity, int *failed, int *err)
+__device__ __forceinline__ bool wait_or_fail(uint32_t mb, uint32_t parity, int *failed, int *err,
+                                             unsigned long long limit_ns = kWaitNs)
 {
-    if (wait_parity(mb, parity)) return true;
+    if (wait_parity(mb, parity, limit_ns)) return true;
     *failed = 1;
     if (err) atomicExch(err, 1);
-    wait_parity(mb, parity);
+    wait_parity(mb, parity, limit_ns);
     return false;
 }
 
@@ -229,7 +230,7 @@ template <int TN>
 __global__ void __launch_bounds__(128)
 conv3_tma_kernel(const __grid_constant__ CUtensorMap tmx, const __half *__restrict__ wp, int H, int W, int C,
                  int cout, int ntn, int nstages, float alpha, float beta, float *y, int ldy, int vec_y, int *err,
-                 Epi epi)
+                 Epi epi, unsigned long long wait_ns, int withhold)
 {
     extern __shared__ unsigned char dyn_raw[];
     __shared__ __align__(8) unsigned long long full[kFwdStages], empty[kFwdStages], done;
@@ -249,9 +250,11 @@ conv3_tma_kernel(const __grid_constant__ CUtensorMap tmx, const __half *__restri
     if (warp == 0 && lane == 0) {
         asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&tmx)) : "memory");
         const __half *wblk = wp + (size_t)nb * nchunks * 18 * TN * 8;
-        for (int i = 0; i < nchunks; ++i) {
+        // withhold (failure-path test only): the producer issues nothing, so no copy is ever in flight
+        for (int i = 0; i < (withhold ? 0 : nchunks); ++i) {
             const int s = i % nstages;
-            if (i >= nstages && !wait_or_fail(smem_u32(&empty[s]), (uint32_t)((i / nstages - 1) & 1), &failed, err))
+            if (i >= nstages &&
+                !wait_or_fail(smem_u32(&empty[s]), (uint32_t)((i / nstages - 1) & 1), &failed, err, wait_ns))
                 break;
             const uint32_t st = base + (uint32_t)(s * kSB), fb = smem_u32(&full[s]);
             expect_tx(fb, kTx);
@@ -261,7 +264,7 @@ conv3_tma_kernel(const __grid_constant__ CUtensorMap tmx, const __half *__restri
     } else if (warp == 1 && lane == 0) {
         for (int i = 0; i < nchunks; ++i) {
             const int s = i % nstages;
-            if (!wait_or_fail(smem_u32(&full[s]), (uint32_t)((i / nstages) & 1), &failed, err)) break;
+            if (!wait_or_fail(smem_u32(&full[s]), (uint32_t)((i / nstages) & 1), &failed, err, wait_ns)) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t st = base + (uint32_t)(s * kSB);
             #pragma unroll
@@ -276,7 +279,7 @@ conv3_tma_kernel(const __grid_constant__ CUtensorMap tmx, const __half *__restri
         commit(smem_u32(&done));    // covers every MMA this thread issued, also after a failure
     }
     __syncwarp();
-    wait_or_fail(smem_u32(&done), 0u, &failed, err);
+    wait_or_fail(smem_u32(&done), 0u, &failed, err, wait_ns);
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
 
@@ -676,7 +679,8 @@ bool blocked_args_ok(const void *p, int N, int H, int W, int C)
 
 template <int TN>
 cudaError_t launch_conv3_tma(const CUtensorMap &tmx, const __half *wp, int N, int H, int W, int C, int cout,
-                             float alpha, float beta, float *y, int ldy, int *err, cudaStream_t s, const Epi &epi)
+                             float alpha, float beta, float *y, int ldy, int *err, cudaStream_t s, const Epi &epi,
+                             unsigned long long wait_ns = kWaitNs, int withhold = 0)
 {
     const int ntn = (cout + TN - 1) / TN;
     const int nchunks = C / kChunk;
@@ -697,7 +701,7 @@ cudaError_t launch_conv3_tma(const CUtensorMap &tmx, const __half *wp, int N, in
         attr_set = true;
     }
     conv3_tma_kernel<TN><<<grid, 128, smem, s>>>(tmx, wp, H, W, C, cout, ntn, nstages, alpha, beta, y, ldy, vec_y,
-                                                 err, epi);
+                                                 err, epi, wait_ns, withhold);
     return cudaGetLastError();
 }
 
@@ -776,28 +780,70 @@ extern "C" int smrt_nn_unpad3_add(const float *gp, int cout, int C, int Cp, floa
     return SMRT_OK;
 }
 
-extern "C" int smrt_nn_conv3_tma(const void *xb, int N, int H, int W, int C, const void *wp, int cout, float alpha,
-                                 float beta, float *y, int ldy, int *err, void *stream)
+namespace {
+
+int conv3_tma_run(const char *name, const void *xb, int N, int H, int W, int C, const void *wp, int cout,
+                  float alpha, float beta, float *y, int ldy, int *err, void *stream, unsigned long long wait_ns,
+                  int withhold)
 {
     if (!blocked_args_ok(xb, N, H, W, C) || C % kChunk != 0 || !wp || !y || cout < 1 || ldy < cout ||
         (reinterpret_cast<uintptr_t>(wp) & 15) != 0 || (H + kTileRows - 1) / kTileRows > 65535 ||
         (long long)N * ((cout + tile_n(cout) - 1) / tile_n(cout)) > 65535)
         return tma_fail(SMRT_ERR_ARG,
-                        "smrt_nn_conv3_tma: bad arguments (N %d H %d W %d C %d cout %d ldy %d; C must be a multiple "
-                        "of 16, xb and wp 16-byte aligned)", N, H, W, C, cout, ldy);
+                        "%s: bad arguments (N %d H %d W %d C %d cout %d ldy %d; C must be a multiple "
+                        "of 16, xb and wp 16-byte aligned)", name, N, H, W, C, cout, ldy);
     CUtensorMap tmx;
     CUresult r = blocked_map(&tmx, xb, N, H, W, C, kHaloPx, kHaloRows, 2);
-    if (r != CUDA_SUCCESS) return tma_fail(SMRT_ERR_CUDA, "smrt_nn_conv3_tma: tensor map rejected (%d)", (int)r);
+    if (r != CUDA_SUCCESS) return tma_fail(SMRT_ERR_CUDA, "%s: tensor map rejected (%d)", name, (int)r);
     cudaStream_t s = (cudaStream_t)stream;
     const __half *w = (const __half *)wp;
     cudaError_t e;
     const int TN = tile_n(cout);
     const Epi plain{nullptr, nullptr, nullptr, nullptr, 0, 0};
-    if (TN == 32) e = launch_conv3_tma<32>(tmx, w, N, H, W, C, cout, alpha, beta, y, ldy, err, s, plain);
-    else if (TN == 64) e = launch_conv3_tma<64>(tmx, w, N, H, W, C, cout, alpha, beta, y, ldy, err, s, plain);
-    else e = launch_conv3_tma<128>(tmx, w, N, H, W, C, cout, alpha, beta, y, ldy, err, s, plain);
-    if (e != cudaSuccess) return tma_fail(SMRT_ERR_CUDA, "smrt_nn_conv3_tma: %s", cudaGetErrorString(e));
+    if (TN == 32)
+        e = launch_conv3_tma<32>(tmx, w, N, H, W, C, cout, alpha, beta, y, ldy, err, s, plain, wait_ns, withhold);
+    else if (TN == 64)
+        e = launch_conv3_tma<64>(tmx, w, N, H, W, C, cout, alpha, beta, y, ldy, err, s, plain, wait_ns, withhold);
+    else
+        e = launch_conv3_tma<128>(tmx, w, N, H, W, C, cout, alpha, beta, y, ldy, err, s, plain, wait_ns, withhold);
+    if (e != cudaSuccess) return tma_fail(SMRT_ERR_CUDA, "%s: %s", name, cudaGetErrorString(e));
     return SMRT_OK;
+}
+
+} // namespace
+
+extern "C" int smrt_nn_conv3_tma(const void *xb, int N, int H, int W, int C, const void *wp, int cout, float alpha,
+                                 float beta, float *y, int ldy, int *err, void *stream)
+{
+    return conv3_tma_run("smrt_nn_conv3_tma", xb, N, H, W, C, wp, cout, alpha, beta, y, ldy, err, stream, kWaitNs,
+                         0);
+}
+
+extern "C" int smrt_nn_conv3_tma_wait_test(const void *xb, int N, int H, int W, int C, const void *wp, int cout,
+                                           float *y, int ldy, int *err, double wait_ms, void *stream)
+{
+    if (!(wait_ms >= 1e-3 && wait_ms <= 1000.0))
+        return tma_fail(SMRT_ERR_ARG, "smrt_nn_conv3_tma_wait_test: wait_ms must lie in [1e-3, 1000] (got %g)",
+                        wait_ms);
+    if (!err) return tma_fail(SMRT_ERR_ARG, "smrt_nn_conv3_tma_wait_test: err is required");
+    return conv3_tma_run("smrt_nn_conv3_tma_wait_test", xb, N, H, W, C, wp, cout, 1.0f, 0.0f, y, ldy, err, stream,
+                         (unsigned long long)(wait_ms * 1e6), 1);
+}
+
+extern "C" int smrt_nn_check(int *err, void *stream)
+{
+    if (!err) return tma_fail(SMRT_ERR_ARG, "smrt_nn_check: err is required");
+    cudaStream_t s = (cudaStream_t)stream;
+    int v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return tma_fail(SMRT_ERR_CUDA, "smrt_nn_check: %s", cudaGetErrorString(e));
+    if (v == 0) return SMRT_OK;
+    e = cudaMemsetAsync(err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return tma_fail(SMRT_ERR_CUDA, "smrt_nn_check: %s", cudaGetErrorString(e));
+    return tma_fail(SMRT_ERR_TIMEOUT, "a tensor-core kernel gave up a bounded wait (error word %d): the blocks "
+                    "concerned skipped their results, so the outputs since the last check are not valid", v);
 }
 
 extern "C" int smrt_nn_conv3_tma_bias_act(const void *xb, int N, int H, int W, int C, const void *wp, int cout,

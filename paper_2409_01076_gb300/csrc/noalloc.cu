@@ -12,8 +12,6 @@
 #include <stdarg.h>
 #include <stdio.h>
 
-#include <mutex>
-
 #include "kernels.cuh"
 
 namespace {
@@ -26,22 +24,18 @@ using smrt::kResidualSums;
 constexpr int kScratchDoubles = kResidualMaxBlocks * kResidualSums + 4;
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-double *g_scratch_addr[kMaxDevices] = {};
-
-// The device address of g_noalloc_scratch on the current device, looked up once
-// per device (host code may not use the symbol's name as an address).
-cudaError_t scratch_address(int dev, double **out)
+// The device address of g_noalloc_scratch in the current context.  Host code may
+// not use the symbol's name as an address.  The lookup allocates nothing and is
+// repeated on every call, so a context that was torn down and created again
+// (cudaDeviceReset) never sees a stale address.  The first lookup on a device
+// loads this module there, which is why the first call on a device should come
+// before any stream capture.
+cudaError_t scratch_address(double **out)
 {
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = static_cast<double *>(p);
-    }
-    *out = g_scratch_addr[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    *out = static_cast<double *>(p);
     return cudaSuccess;
 }
 
@@ -200,7 +194,6 @@ extern "C" SMRT_API int smrt_residual_noalloc(const double *f, int nx, int ny, d
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
-    if (dev < 0 || dev >= kMaxDevices) return arg_error("smrt_residual_noalloc: device %d not supported", dev);
     cudaPointerAttributes at;
     e = cudaPointerGetAttributes(&at, f);
     if (e != cudaSuccess || (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != dev) {
@@ -216,7 +209,7 @@ extern "C" SMRT_API int smrt_residual_noalloc(const double *f, int nx, int ny, d
     cudaGetLastError();
 
     double *scratch = nullptr;
-    if ((e = scratch_address(dev, &scratch)) != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress");
+    if ((e = scratch_address(&scratch)) != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress");
 
     smrt::HostParams hp;
     hp.nx = nx;

@@ -82,6 +82,18 @@ def smrt_nn_conv3_tma(xb, nhwc, wp, y, cout, alpha=1.0, beta=0.0, err=None):
                                          float(beta), _p(y), int(y.shape[-1]), _p(err), _s()))
 
 
+def smrt_nn_check(err):
+    """Raises SmrtError(SMRT_ERR_TIMEOUT) (and resets err) if a tensor-core wait gave up; waits for the stream."""
+    _check(_lib.load().smrt_nn_check(_p(err), _s()))
+
+
+def smrt_nn_conv3_tma_wait_test(xb, nhwc, wp, y, cout, err, wait_ms=1.0):
+    """Failure-path test hook: smrt_nn_conv3_tma with a withheld producer and a wait limit of wait_ms."""
+    n, h, w, c = nhwc
+    _check(_lib.load().smrt_nn_conv3_tma_wait_test(_p(xb), int(n), int(h), int(w), int(c), _p(wp), int(cout), _p(y),
+                                                   int(y.shape[-1]), _p(err), float(wait_ms), _s()))
+
+
 def smrt_nn_conv3_tma_bias_act(xb, nhwc, wp, cout, bias, act, z, a, ab, err=None):
     """Forward convolution with bias and activation in the epilogue; z, a: N*H*W rows of cout float32 or
     None; ab: blocked halves or None."""

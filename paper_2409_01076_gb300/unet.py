@@ -112,8 +112,13 @@ class UNet:
             K.smrt_nn_gemm(transA, transB, M, N, Kd, alpha, A, lda, B, ldb, beta, C, ldc, split)
 
     def gemm_timeouts(self) -> int:
-        """Number of tensor-core wait timeouts seen so far (0 unless the hardware stalled)."""
+        """Tensor-core wait timeouts recorded since the last check (0 unless the hardware stalled)."""
         return int(self._gemm_err.item())
+
+    def check_timeouts(self) -> None:
+        """Raises SmrtError(SMRT_ERR_TIMEOUT) if a tensor-core kernel gave up a bounded wait since the
+        last check (its blocks skipped their outputs); waits for the current stream."""
+        K.smrt_nn_check(self._gemm_err)
 
     # ---- parameters --------------------------------------------------------------------
     def load_numpy(self, params: dict) -> None:
@@ -416,7 +421,10 @@ class UNet:
         return y
 
     def adam_step(self, lr: float, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8) -> bool:
-        """Applies the accumulated gradients; returns False (and lowers the loss scale) on overflow."""
+        """Applies the accumulated gradients; returns False (and lowers the loss scale) on overflow.
+        Raises SmrtError(SMRT_ERR_TIMEOUT), before touching the parameters, if a tensor-core wait of
+        the forward or backward pass gave up."""
+        self.check_timeouts()
         self.step_count += 1
         self._found_inf.zero_()
         f = self._flat      # the padding between views holds zeros in all four buffers and stays zero
@@ -457,7 +465,9 @@ class UNet:
         return float(self._loss.item())
 
     def predict(self, x):
-        return self.forward(x, None)
+        y = self.forward(x, None)
+        self.check_timeouts()
+        return y
 
 
 def input_grid(res, h: int, w: int, device: str = "cuda"):

@@ -210,3 +210,35 @@ def test_tma_kernels_reject_unsupported_arguments():
         S.smrt_nn_conv3_wgrad_tma(xb, (1, 4, 4, 16), xb, 12, gw)
     assert ei.value.status == S.SMRT_ERR_ARG
     assert S.smrt_nn_pack3_halves(8, 24) == -1
+
+
+def test_wait_timeout_is_reported_and_the_next_call_runs():
+    """Failure path of the bounded tensor-core waits: with the TMA producer withholding every copy
+    and a 1 ms limit, every block's wait runs out (nothing is ever in flight).  smrt_nn_check then
+    returns SMRT_ERR_TIMEOUT and resets the error word, the output is untouched, tensor memory was
+    released (the next launch allocates it again), and the next ordinary call is correct -- twice."""
+    import torch
+    n, h, w, C, cout = 2, 37, 21, 32, 40          # 3 x 3 x 2 x 2 = 36 blocks, two output tiles each
+    r = _rng(4242)
+    x = r.normal(size=(n, h, w, C)).astype(np.float16)
+    wt = r.normal(size=(cout, 9 * C)).astype(np.float16)
+    xb = torch.tensor(_blocked(x), device="cuda")
+    wp = torch.empty(S.smrt_nn_pack3_halves(cout, C), dtype=torch.float16, device="cuda")
+    S.smrt_nn_pack3(torch.tensor(wt, device="cuda"), C, wp)
+    exp = U.im2col3(x.astype(np.float64)) @ wt.astype(np.float64).T
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for _ in range(2):
+        y = torch.full((n * h * w, cout), float("nan"), device="cuda")
+        S.smrt_nn_conv3_tma_wait_test(xb, (n, h, w, C), wp, y, cout, err, wait_ms=1.0)
+        with pytest.raises(S.SmrtError) as ei:
+            S.smrt_nn_check(err)
+        assert ei.value.status == S.SMRT_ERR_TIMEOUT
+        assert int(err.item()) == 0                       # the check resets the word
+        assert bool(torch.isnan(y).all())                 # blocks that gave up wrote nothing
+        S.smrt_nn_conv3_tma(xb, (n, h, w, C), wp, y, cout, 1.0, 0.0, err)
+        S.smrt_nn_check(err)                              # no timeout on the ordinary call
+        got = y.cpu().numpy()
+        assert np.abs(got - exp).max() <= 1e-4 * np.abs(exp).max()
+    with pytest.raises(S.SmrtError) as ei:
+        S.smrt_nn_conv3_tma_wait_test(xb, (n, h, w, C), wp, y, cout, err, wait_ms=0.0)
+    assert ei.value.status == S.SMRT_ERR_ARG
