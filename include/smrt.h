@@ -29,7 +29,11 @@
  * - Pointers may be host memory (pageable or pinned) or device memory of the
  *   current CUDA device; the library tells them apart with
  *   cudaPointerGetAttributes.  Device-pointer calls run on the handle's
- *   stream; host-pointer calls return after the copy completed.
+ *   stream; host-pointer calls return after the transfer completed.  Page-locked
+ *   host memory (cudaHostAlloc / cudaHostRegister, e.g. pinned torch tensors)
+ *   is read or written by the kernels themselves over the host link, with no
+ *   staging copy, so the transfer overlaps the arithmetic; pageable host memory
+ *   goes through a device staging buffer in chunks of up to 64 MB.
  * - The canonical state f(t) is the post-streaming, pre-collision field, i.e.
  *   the left-hand side of Eq. (SmrtLBM-1) after t updates; rho(t), u(t) are its
  *   moments (Eq. fea-0).  t counts applications of the update.
@@ -90,7 +94,21 @@ enum smrt_option {
                                       0: smrt_step only enqueues                           */
     SMRT_OPT_MEM_LIMIT = 6,   /* bytes the handle may allocate on the device; 0 = no limit;
                                  only before the state is first touched                  */
-    SMRT_OPT_TAU = 7          /* change tau (> 0.5); any time                              */
+    SMRT_OPT_TAU = 7,         /* change tau (> 0.5); any time                              */
+    SMRT_OPT_ROUNDING = 8     /* SMRT_ROUND_*: how F16/BF16 storage rounds; any time       */
+};
+/* Rounding of the stored offsets in the 16-bit formats (FP32 and FP64 storage keep the
+ * arithmetic's own result and ignore it).  NEAREST (default): round to nearest even.  In a
+ * smooth, slowly changing flow neighbouring nodes then round the same way step after step, a
+ * coherent error that grows to ~9e-2 U (FP16) and ~0.45 U (BF16) after 20,000 updates of a
+ * 1024^2 cavity at Re 5,000.  STOCHASTIC: each stored value rounds up or down with the
+ * probabilities that make its expected value exact, from counter-based random bits keyed by
+ * (node, population, t) -- reproducible, identical in both layouts, restored with t from a
+ * checkpoint -- so the rounding errors are uncorrelated and largely average out, at the cost
+ * of ~60 more integer operations per node. */
+enum smrt_rounding {
+    SMRT_ROUND_NEAREST = 0,
+    SMRT_ROUND_STOCHASTIC = 1
 };
 enum smrt_collision {
     SMRT_COLLISION_SMRT = 0,    /* Eq. (SmrtLBM-1)                                   */
@@ -174,9 +192,11 @@ SMRT_API int smrt_residual(smrt_t *h, double *r, double *sums);
  *
  * Scratch: the per-block partial sums live in one file-scope device array of
  * 1216 x 5 + 4 doubles (48,672 bytes), which every GPU that loads the library
- * holds until the process exits.  The first call on each device looks up that
- * array's device address (cudaGetSymbolAddress) with the device current; make
- * that first call before any stream capture.  Every call on a device shares the
+ * holds until the process exits.  Every call looks up that array's device
+ * address (cudaGetSymbolAddress) in the current context, so a context that was
+ * reset and created again is handled; the first call on a device also loads the
+ * library's device code there, so make that first call before any stream
+ * capture.  Every call on a device shares the
  * array and leaves its contents behind; nothing in it needs to start at zero
  * (each call writes every slot it later reads).  Calls whose work overlaps on
  * the GPU -- on different streams, or from different host threads -- race on
@@ -246,7 +266,9 @@ SMRT_API int smrt_batch_set_stream(smrt_batch_t *b, void *stream);
 /* Times each candidate tile shape of the work-list kernel (nodes per thread x
  * threads per block, with or without a 64-register bound, each without (index k)
  * and with (index k + 5 for FP32 storage, k + 4 for FP64) the edge column groups
- * of the two-buffer layout in the vector path; FP32: 10 candidates, FP64: 8) on
+ * of the two-buffer layout in the vector path; then row-segmented shapes, whose
+ * warps cover several rows of a narrow lattice at once (indices 10 to 12 for
+ * FP32, 8 for FP64); FP32: 13 candidates, FP64: 9) on
  * `steps` steps of this batch, run on a copy of the state so no lattice advances,
  * and keeps the fastest; *choice (may be NULL) receives its index.  Allocates one
  * scratch copy of the populations for the duration. */

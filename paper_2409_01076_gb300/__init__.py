@@ -21,7 +21,8 @@ SMRT_OK, SMRT_ERR_ARG, SMRT_ERR_OOM, SMRT_ERR_CUDA = 0, -1, -2, -3
 SMRT_ERR_DIVERGED, SMRT_ERR_TIMEOUT, SMRT_ERR_STATE = -4, -5, -6
 
 SMRT_OPT_COLLISION, SMRT_OPT_TAU_S, SMRT_OPT_LAYOUT, SMRT_OPT_PRECISION = 1, 2, 3, 4
-SMRT_OPT_CHECK_DIVERGENCE, SMRT_OPT_MEM_LIMIT, SMRT_OPT_TAU = 5, 6, 7
+SMRT_OPT_CHECK_DIVERGENCE, SMRT_OPT_MEM_LIMIT, SMRT_OPT_TAU, SMRT_OPT_ROUNDING = 5, 6, 7, 8
+SMRT_ROUND_NEAREST, SMRT_ROUND_STOCHASTIC = 0, 1
 SMRT_COLLISION_SMRT, SMRT_COLLISION_SRT, SMRT_COLLISION_TWO_TAU = 0, 1, 2
 SMRT_LAYOUT_AB, SMRT_LAYOUT_AA = 0, 1
 SMRT_PREC_F64, SMRT_PREC_F32, SMRT_PREC_F16, SMRT_PREC_BF16 = 0, 1, 2, 3

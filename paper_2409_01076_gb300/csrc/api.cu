@@ -45,6 +45,7 @@ struct smrt_t {
     int layout = SMRT_LAYOUT_AB;
     int prec = SMRT_PREC_F64;
     int check_div = 1;
+    int rounding = SMRT_ROUND_NEAREST;
     double mem_limit = 0.0;
     cudaStream_t stream = nullptr;
 
@@ -156,6 +157,8 @@ HostParams host_params(const smrt_t *h)
     p.tau_s = h->tau_s;
     p.u_lid = h->u_lid;
     p.flag = h->d_flag;
+    p.rounding = h->rounding;
+    p.t = h->t;
     return p;
 }
 
@@ -266,7 +269,11 @@ int ensure_stage(smrt_t *h, int planes)
 }
 
 // 0: host memory, 1: device memory of the handle's device, -1: unusable.
-int classify(smrt_t *h, const void *ptr)
+// Where a caller's array lives: 1 = memory of the handle's device, 2 = page-locked host memory
+// the device addresses directly (its device address goes to *dptr; kernels then read or write
+// it over the host link, with no staging copy), 0 = other host memory (staged in chunks),
+// -1 = another device's memory.
+int classify(smrt_t *h, const void *ptr, const void **dptr = nullptr)
 {
     cudaPointerAttributes at;
     cudaError_t e = cudaPointerGetAttributes(&at, ptr);
@@ -276,6 +283,10 @@ int classify(smrt_t *h, const void *ptr)
     }
     if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)
         return (at.device == h->device) ? 1 : -1;
+    if (at.type == cudaMemoryTypeHost && at.devicePointer) {
+        if (dptr) *dptr = at.devicePointer;
+        return 2;
+    }
     return 0;
 }
 
@@ -364,6 +375,11 @@ int smrt_set_option(smrt_t *h, int key, double value)
         if (!(value >= 0.0) || !isfinite(value)) return fail(h, SMRT_ERR_ARG, "MEM_LIMIT must be >= 0");
         h->mem_limit = value;
         return SMRT_OK;
+    case SMRT_OPT_ROUNDING:
+        if (value != SMRT_ROUND_NEAREST && value != SMRT_ROUND_STOCHASTIC)
+            return fail(h, SMRT_ERR_ARG, "ROUNDING: unknown %g", value);
+        h->rounding = (int)value;
+        return SMRT_OK;
     default:
         return fail(h, SMRT_ERR_ARG, "unknown option key %d", key);
     }
@@ -380,6 +396,7 @@ int smrt_get_option(const smrt_t *h, int key, double *value)
     case SMRT_OPT_PRECISION: *value = h->prec; return SMRT_OK;
     case SMRT_OPT_CHECK_DIVERGENCE: *value = h->check_div; return SMRT_OK;
     case SMRT_OPT_MEM_LIMIT: *value = h->mem_limit; return SMRT_OK;
+    case SMRT_OPT_ROUNDING: *value = h->rounding; return SMRT_OK;
     default: return fail(const_cast<smrt_t *>(h), SMRT_ERR_ARG, "unknown option key %d", key);
     }
 }
@@ -416,6 +433,7 @@ int smrt_step(smrt_t *h, long long n)
     HostParams p = host_params(h);
     for (long long s = 0; s < n; ++s) {
         cudaError_t e;
+        p.t = h->t;
         if (h->layout == SMRT_LAYOUT_AB) {
             e = T.step(h->collision, MODE_AB, h->buf[h->cur], h->buf[1 - h->cur], p, h->stream);
             if (e == cudaSuccess) h->cur = 1 - h->cur;
@@ -440,11 +458,12 @@ int smrt_macros(smrt_t *h, double *rho, double *u)
     const KernelTable &T = table_for(h->prec);
     HostParams p = host_params(h);
     const void *state = h->buf[h->cur];
-    int kr = rho ? classify(h, rho) : -2, ku = u ? classify(h, u) : -2;
+    const void *drho = rho, *du = u;
+    int kr = rho ? classify(h, rho, &drho) : -2, ku = u ? classify(h, u, &du) : -2;
     if (kr == -1 || ku == -1) return fail(h, SMRT_ERR_ARG, "smrt_macros: pointer on another device");
-    const bool dev = (kr != 0) && (ku != 0);
-    if (dev) {
-        CUDA_TRY(h, T.macros(current_mode(h), state, rho, u, 0, h->ny, p, h->stream));
+    if (kr != 0 && ku != 0) {            // device memory, or page-locked host memory written directly
+        CUDA_TRY(h, T.macros(current_mode(h), state, (double *)drho, (double *)du, 0, h->ny, p, h->stream));
+        if (kr == 2 || ku == 2) CUDA_TRY(h, cudaStreamSynchronize(h->stream));
         return SMRT_OK;
     }
     // host outputs (or mixed): go through the staging buffer, 3 planes per chunk
@@ -508,10 +527,12 @@ int smrt_get_f(smrt_t *h, double *f)
     const KernelTable &T = table_for(h->prec);
     HostParams p = host_params(h);
     const void *state = h->buf[h->cur];
-    int k = classify(h, f);
+    const void *df = f;
+    int k = classify(h, f, &df);
     if (k == -1) return fail(h, SMRT_ERR_ARG, "smrt_get_f: pointer on another device");
-    if (k == 1) {
-        CUDA_TRY(h, T.get_f(current_mode(h), state, f, 0, h->ny, p, h->stream));
+    if (k != 0) {
+        CUDA_TRY(h, T.get_f(current_mode(h), state, (double *)df, 0, h->ny, p, h->stream));
+        if (k == 2) CUDA_TRY(h, cudaStreamSynchronize(h->stream));
         return SMRT_OK;
     }
     if ((rc = ensure_stage(h, 9)) != SMRT_OK) return rc;
@@ -537,11 +558,13 @@ int smrt_set_f(smrt_t *h, const double *f)
     const KernelTable &T = table_for(h->prec);
     HostParams p = host_params(h);
     void *state = h->buf[h->cur];
-    int k = classify(h, f);
+    const void *df = f;
+    int k = classify(h, f, &df);
     if (k == -1) return fail(h, SMRT_ERR_ARG, "smrt_set_f: pointer on another device");
     CUDA_TRY(h, cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream));
-    if (k == 1) {
-        CUDA_TRY(h, T.set_f(current_mode(h), state, f, 0, h->ny, p, h->stream));
+    if (k != 0) {
+        CUDA_TRY(h, T.set_f(current_mode(h), state, (const double *)df, 0, h->ny, p, h->stream));
+        if (k == 2) CUDA_TRY(h, cudaStreamSynchronize(h->stream));
         return SMRT_OK;
     }
     if ((rc = ensure_stage(h, 9)) != SMRT_OK) return rc;
@@ -567,11 +590,14 @@ int smrt_init_macros(smrt_t *h, const double *rho, const double *u)
     const KernelTable &T = table_for(h->prec);
     HostParams p = host_params(h);
     void *state = h->buf[h->cur];
-    int kr = classify(h, rho), ku = classify(h, u);
+    const void *drho = rho, *du = u;
+    int kr = classify(h, rho, &drho), ku = classify(h, u, &du);
     if (kr == -1 || ku == -1) return fail(h, SMRT_ERR_ARG, "smrt_init_macros: pointer on another device");
     CUDA_TRY(h, cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream));
-    if (kr == 1 && ku == 1) {
-        CUDA_TRY(h, T.init_macros(current_mode(h), state, rho, u, 0, h->ny, p, h->stream));
+    if (kr != 0 && ku != 0) {            // device memory, or page-locked host memory read directly
+        CUDA_TRY(h, T.init_macros(current_mode(h), state, (const double *)drho, (const double *)du, 0, h->ny, p,
+                                  h->stream));
+        if (kr == 2 || ku == 2) CUDA_TRY(h, cudaStreamSynchronize(h->stream));
         return SMRT_OK;
     }
     if ((rc = ensure_stage(h, 3)) != SMRT_OK) return rc;

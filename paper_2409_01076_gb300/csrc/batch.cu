@@ -53,7 +53,7 @@ __device__ __forceinline__ void cp_async_wait_all()
 // compiler takes what the step needs and fewer blocks are resident.
 // EDGE: the two-buffer step also runs the edge column groups in the vector path (their geometry
 // must say so); without it those columns stay in the band and the vector path carries no edge code.
-template <int PREC, int KIND, int MODE, int VEC, int BX, bool CAP, bool EDGE>
+template <int PREC, int KIND, int MODE, int VEC, int BX, bool CAP, bool EDGE, bool ROWSEG = false>
 __global__ void __launch_bounds__(BX, CAP ? 1024 / BX : 1)
 batch_step_kernel(const typename Prec<PREC>::R *src, typename Prec<PREC>::R *dst,
                   const BatchCav<typename Prec<PREC>::C> *__restrict__ cav, const int2 *__restrict__ work,
@@ -89,7 +89,7 @@ batch_step_kernel(const typename Prec<PREC>::R *src, typename Prec<PREC>::R *dst
             for (int k = threadIdx.x; k < kWords; k += BX) cp_async8(&rec[buf ^ 1][k], g + k);
         }
         const Cav &r = *reinterpret_cast<const Cav *>(rec[buf]);
-        step_block<PREC, KIND, MODE, VEC, BX, EDGE>(src + r.offset, dst + r.offset, r.p, r.geo, w.y);
+        step_block<PREC, KIND, MODE, VEC, BX, EDGE, ROWSEG>(src + r.offset, dst + r.offset, r.p, r.geo, w.y);
         if (!next) break;
         if (swap) {
             cp_async_wait_all();
@@ -124,10 +124,8 @@ batch_residual_kernel(const typename Prec<PREC>::R *state, const BatchCav<typena
         if (i < L.p.nx) {
             typename Prec<PREC>::C g[9];
             pull_canonical<PREC, MODE>(state + L.offset, L.p, i, j, g);
-            double gd[9], rr, ux, uy;
-            #pragma unroll
-            for (int a = 0; a < 9; ++a) gd[a] = (double)g[a];
-            moments_d(gd, rr, ux, uy);
+            double rr, ux, uy;
+            moments_any(g, rr, ux, uy);
             double2 *up = uprev + L.uoff + (size_t)j * L.p.nx + i;
             const double2 old = *up;
             const double dx = ux - (double)old.x, dy = uy - (double)old.y;
@@ -190,41 +188,50 @@ batch_finish_kernel(const int *__restrict__ act, const int *__restrict__ rpre, c
 // (index k) or with (index k + nbase) the edge column groups in the vector path.  Measured on one
 // GB300: the edge variant is faster on batches of lattices up to ~1024 wide (256^2: +20 %), the
 // plain one on batches of 4096^2 lattices (the edge code costs the vector path a few per cent there).
+// Row-segmented shapes (index 2 * nbase + m) cut the interior into row segments of the fewest lanes
+// that cover a row (step_geom_seg): a warp works on 2 rows of a 128-wide lattice (FP32) or 4 of a
+// 64-wide one at once, where a block of the other shapes leaves most of its lanes idle.
 struct Shape {
     int vec, bx;
-    bool cap;   // 64-register bound
-    bool edge;  // edge column groups in the vector path (two-buffer layout)
+    bool cap;     // 64-register bound
+    bool edge;    // edge column groups in the vector path (two-buffer layout)
+    bool rowseg;  // row-segmented interior blocks
 };
 template <int PREC> struct Shapes;
 template <> struct Shapes<SMRT_PREC_F32> {
-    static constexpr int nbase = 5, n = 2 * nbase;
+    static constexpr int nbase = 5, nseg = 3, n = 2 * nbase + nseg;
     static Shape at(int k)
     {
-        const Shape s[nbase] = {{4, 128, true, false}, {4, 64, true, false}, {4, 256, true, false},
-                                {2, 128, true, false}, {4, 128, false, false}};
+        const Shape s[nbase] = {{4, 128, true, false, false}, {4, 64, true, false, false},
+                                {4, 256, true, false, false}, {2, 128, true, false, false},
+                                {4, 128, false, false, false}};
+        const Shape g[nseg] = {{4, 128, true, true, true}, {4, 128, false, true, true}, {4, 256, true, true, true}};
+        if (k >= 2 * nbase) return g[k - 2 * nbase];
         Shape r = s[k % nbase];
         r.edge = k >= nbase;
         return r;
     }
 };
 template <> struct Shapes<SMRT_PREC_F64> {
-    static constexpr int nbase = 4, n = 2 * nbase;
+    static constexpr int nbase = 4, nseg = 1, n = 2 * nbase + nseg;
     static Shape at(int k)
     {
-        const Shape s[nbase] = {{2, 128, true, false}, {2, 64, true, false}, {1, 128, true, false},
-                                {2, 128, false, false}};
+        const Shape s[nbase] = {{2, 128, true, false, false}, {2, 64, true, false, false},
+                                {1, 128, true, false, false}, {2, 128, false, false, false}};
+        const Shape g[nseg] = {{2, 128, true, true, true}};
+        if (k >= 2 * nbase) return g[k - 2 * nbase];
         Shape r = s[k % nbase];
         r.edge = k >= nbase;
         return r;
     }
 };
 
-template <int PREC, int KIND, int MODE, int VEC, int BX, bool CAP = true, bool EDGE = false>
+template <int PREC, int KIND, int MODE, int VEC, int BX, bool CAP = true, bool EDGE = false, bool ROWSEG = false>
 cudaError_t launch_batch_step_shape(const void *src, void *dst, const void *cav, const int2 *work,
                                     const int *counts, int sms, cudaStream_t s)
 {
     using P = Prec<PREC>;
-    auto kern = batch_step_kernel<PREC, KIND, MODE, VEC, BX, CAP, EDGE>;
+    auto kern = batch_step_kernel<PREC, KIND, MODE, VEC, BX, CAP, EDGE, ROWSEG>;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BX, 0);
     if (e != cudaSuccess) return e;
@@ -252,6 +259,12 @@ cudaError_t launch_batch_step_m(int shape, const void *src, void *dst, const voi
         case 7: return launch_batch_step_shape<PREC, KIND, MODE, 4, 256, true, E>(src, dst, cav, work, counts, sms, s);
         case 8: return launch_batch_step_shape<PREC, KIND, MODE, 2, 128, true, E>(src, dst, cav, work, counts, sms, s);
         case 9: return launch_batch_step_shape<PREC, KIND, MODE, 4, 128, false, E>(src, dst, cav, work, counts, sms, s);
+        case 10:
+            return launch_batch_step_shape<PREC, KIND, MODE, 4, 128, true, E, true>(src, dst, cav, work, counts, sms, s);
+        case 11:
+            return launch_batch_step_shape<PREC, KIND, MODE, 4, 128, false, E, true>(src, dst, cav, work, counts, sms, s);
+        case 12:
+            return launch_batch_step_shape<PREC, KIND, MODE, 4, 256, true, E, true>(src, dst, cav, work, counts, sms, s);
         }
     } else {
         switch (shape) {
@@ -263,6 +276,8 @@ cudaError_t launch_batch_step_m(int shape, const void *src, void *dst, const voi
         case 5: return launch_batch_step_shape<PREC, KIND, MODE, 2, 64, true, E>(src, dst, cav, work, counts, sms, s);
         case 6: return launch_batch_step_shape<PREC, KIND, MODE, 1, 128, true, E>(src, dst, cav, work, counts, sms, s);
         case 7: return launch_batch_step_shape<PREC, KIND, MODE, 2, 128, false, E>(src, dst, cav, work, counts, sms, s);
+        case 8:
+            return launch_batch_step_shape<PREC, KIND, MODE, 2, 128, true, E, true>(src, dst, cav, work, counts, sms, s);
         }
     }
     return cudaErrorInvalidValue;
@@ -327,6 +342,11 @@ StepGeom geom_for(int shape, int nx, int ny, bool edge_in)
 {
     Shape sh = Shapes<PREC>::at(shape);
     edge_in = edge_in && sh.edge;
+    if (sh.rowseg) {
+        if (sh.vec == 4 && sh.bx == 256) return step_geom_seg<4, 256>(nx, ny, edge_in);
+        if (sh.vec == 4) return step_geom_seg<4, 128>(nx, ny, edge_in);
+        return step_geom_seg<2, 128>(nx, ny, edge_in);
+    }
     if (sh.vec == 4 && sh.bx == 128) return step_geom<4, 128>(nx, ny, edge_in);
     if (sh.vec == 4 && sh.bx == 64) return step_geom<4, 64>(nx, ny, edge_in);
     if (sh.vec == 4 && sh.bx == 256) return step_geom<4, 256>(nx, ny, edge_in);

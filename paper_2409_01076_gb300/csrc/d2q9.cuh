@@ -62,12 +62,26 @@ template <> struct Prec<SMRT_PREC_F32> {
     static __device__ __forceinline__ C to_c(R r) { return r; }
     static __device__ __forceinline__ R to_r(C c) { return c; }
 };
+// Stochastic rounding (to_r_sr): c goes to one of its two neighbours in the storage format, the
+// farther one with probability equal to the distance from the nearer one (in units of their
+// spacing), so that the expected stored value is c itself.  r supplies 16 uniform bits.
+// BF16 keeps the upper 16 bits of the float: adding r to the lower 16 and truncating is exactly
+// that.  IEEE half keeps 10 of float's 23 mantissa bits where it is normal (|c| >= 2^-14): add 13 of
+// the bits below them and truncate; below that its spacing is fixed at 2^-24, so a uniform fraction
+// of 2^-24 is added before truncating.  Truncation is toward zero on the magnitude, so the rounding
+// is symmetric in the sign.
 template <> struct Prec<SMRT_PREC_F16> {
     using R = unsigned short;
     using C = float;
     static constexpr bool kExactWeights = false;
     static __device__ __forceinline__ C to_c(R r) { return __half2float(__ushort_as_half(r)); }
     static __device__ __forceinline__ R to_r(C c) { return __half_as_ushort(__float2half_rn(c)); }
+    static __device__ __forceinline__ R to_r_sr(C c, uint32_t r)
+    {
+        const float yn = __uint_as_float(__float_as_uint(c) + (r & 0x1FFFu));
+        const float ys = c + copysignf(__uint_as_float(0x33800000u) * ((float)(r & 0xFFFFu) * (1.0f / 65536.0f)), c);
+        return __half_as_ushort(__float2half_rz(fabsf(c) >= 6.103515625e-05f ? yn : ys));
+    }
 };
 template <> struct Prec<SMRT_PREC_BF16> {
     using R = unsigned short;
@@ -75,7 +89,42 @@ template <> struct Prec<SMRT_PREC_BF16> {
     static constexpr bool kExactWeights = false;
     static __device__ __forceinline__ C to_c(R r) { return __bfloat162float(__ushort_as_bfloat16(r)); }
     static __device__ __forceinline__ R to_r(C c) { return __bfloat16_as_ushort(__float2bfloat16_rn(c)); }
+    static __device__ __forceinline__ R to_r_sr(C c, uint32_t r)
+    {
+        return (R)((__float_as_uint(c) + (r & 0xFFFFu)) >> 16);
+    }
 };
+
+// Counter-based random bits of the stochastic rounding: a 32-bit mix of the node's linear index and
+// the step's salt (two multiply-xorshift rounds), and from it 16 bits per population by an odd
+// multiplier per population (the upper half of the product).  Keyed by (node, population, time), so
+// every layout and every code path that stores f*_a(x, t) draws the same bits.
+__device__ __forceinline__ uint32_t sr_node_hash(uint32_t node, uint32_t salt)
+{
+    uint32_t h = node * 0x9E3779B1u + salt;
+    h ^= h >> 16;
+    h *= 0x7FEB352Du;
+    h ^= h >> 15;
+    h *= 0x846CA68Bu;
+    h ^= h >> 16;
+    return h;
+}
+__device__ __forceinline__ uint32_t sr_pop_bits(uint32_t h, int a)
+{
+    const uint32_t m = a == 0 ? 0x9E3779B1u : a == 1 ? 0x85EBCA77u : a == 2 ? 0xC2B2AE3Du : a == 3 ? 0x27D4EB2Fu
+                     : a == 4 ? 0x165667B1u : a == 5 ? 0xD3A2646Du : a == 6 ? 0xFD7046C5u : a == 7 ? 0xB55A4F09u
+                     : 0x2545F491u;
+    return (h * m) >> 16;
+}
+// The salt of the step that starts from time t (host side).
+inline uint32_t sr_salt(long long t)
+{
+    uint64_t x = (uint64_t)t * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+    x ^= x >> 31;
+    x *= 0xBF58476D1CE4E5B9ull;
+    x ^= x >> 29;
+    return (uint32_t)(x >> 16);
+}
 
 // ---- kernel parameters --------------------------------------------------------
 enum { SIDE_LEFT = 0, SIDE_RIGHT = 1, SIDE_BOTTOM = 2, SIDE_TOP = 3 };
@@ -93,6 +142,7 @@ struct Params {
     C trt4;             // (1/tau_s - 1/tau) / 4, two-relaxation-time form
     C corr[4][9];       // moving-wall term 6 w_a (e_a . u_w(side)) added to a wall-pulled offset
     int *flag;          // divergence flag (bit 0)
+    uint32_t salt;      // stochastic rounding: the salt of this launch's time step
 };
 
 template <class C>
@@ -120,6 +170,7 @@ inline Params<C> make_params(const HostParams &h)
             p.corr[s][a] = C(6.0 * wgt<double>(a) * (ex(a) * wx + ey(a) * wy));
     }
     p.flag = h.flag;
+    p.salt = sr_salt(h.t);
     return p;
 }
 

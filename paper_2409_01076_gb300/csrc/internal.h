@@ -32,6 +32,8 @@ struct HostParams {
     unsigned bc;
     double tau, tau_s, u_lid;
     int *flag;          // device divergence flag
+    int rounding = 0;   // SMRT_ROUND_*: how 16-bit storage rounds the stored offsets
+    long long t = 0;    // the time of the state a step or residual launch starts from
 };
 
 // Device scratch the auxiliary launchers may use (owned by the caller).

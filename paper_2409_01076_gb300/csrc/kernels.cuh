@@ -29,8 +29,12 @@ constexpr unsigned kFull = 0xffffffffu;
 struct StepGeom {
     int L, R;            // interior columns [L, R), multiples of VEC
     int bpr;             // interior blocks per row
-    int n_int_blocks;    // bpr * (ny - 2)
+    int n_int_blocks;    // bpr * (ny - 2), or the row-segment blocks (below)
     long long n_edge;    // band nodes
+    // row-segmented blocks only (step_block<..., ROWSEG = true>): a row segment is `seg` lanes
+    // (a power of two <= 32) owning seg * VEC consecutive columns; a row holds `spr` segments,
+    // the interior `tasks` = (ny - 2) * spr of them, and a block of BX threads takes BX / seg.
+    int seg_log2, spr, tasks;
 };
 
 // edge_in (the two-buffer layout only): the first and, when nx % VEC == 0, the last VEC-wide
@@ -58,13 +62,36 @@ inline StepGeom step_geom(int nx, int ny, bool edge_in)
     g.n_int_blocks = g.bpr * rows;
     long long bw = (long long)L + (long long)(nx - R);
     g.n_edge = (ny >= 2 ? 2LL * nx : (long long)nx) + (long long)rows * bw;
+    g.seg_log2 = 5;
+    g.spr = 0;
+    g.tasks = 0;
     return g;
 }
 
-// vals[k] = row[i0 + k + s], s in {-1, 0, +1}, for a thread owning nodes i0..i0+VEC-1.
+// Row-segmented geometry: the same interior and band as step_geom, but the interior is cut into
+// row segments of the fewest lanes (a power of two up to a warp) that cover a row, so that a warp
+// works on 32 / seg rows of a narrow lattice at once instead of leaving lanes idle.
+template <int VEC, int BX>
+inline StepGeom step_geom_seg(int nx, int ny, bool edge_in)
+{
+    StepGeom g = step_geom<VEC, BX>(nx, ny, edge_in);
+    const int groups = (g.R + VEC - 1) / VEC;        // VEC-wide column groups covering [0, R)
+    int lg = 0;
+    while ((1 << lg) < groups && lg < 5) ++lg;
+    g.seg_log2 = lg;
+    g.spr = (groups + (1 << lg) - 1) >> lg;
+    const int rows = ny - 2 > 0 ? ny - 2 : 0;
+    g.tasks = (g.R > g.L) ? rows * g.spr : 0;
+    const int per_block = BX >> lg;
+    g.n_int_blocks = (g.tasks + per_block - 1) / per_block;
+    return g;
+}
+
+// vals[k] = row[i0 + k + s], s in {-1, 0, +1}, for a thread owning nodes i0..i0+VEC-1.  The lanes
+// of one row segment (seg consecutive lanes, a power of two <= 32) own consecutive nodes.
 template <int PREC, int VEC>
 __device__ __forceinline__ void load_row(const typename Prec<PREC>::R *row, int i0, int s, int lane,
-                                         bool loader, int nx, typename Prec<PREC>::C vals[VEC])
+                                         bool loader, int nx, typename Prec<PREC>::C vals[VEC], int seg = 32)
 {
     using P = Prec<PREC>;
     using R = typename P::R;
@@ -86,89 +113,132 @@ __device__ __forceinline__ void load_row(const typename Prec<PREC>::R *row, int 
         #pragma unroll
         for (int k = 0; k < VEC; ++k) vals[k] = c[k];
     } else if (s < 0) {
-        C left = __shfl_up_sync(kFull, c[VEC - 1], 1);
-        if (lane == 0) left = (loader && i0 >= 1) ? P::to_c(row[i0 - 1]) : C(0);
+        C left = __shfl_up_sync(kFull, c[VEC - 1], 1, seg);
+        if ((lane & (seg - 1)) == 0) left = (loader && i0 >= 1) ? P::to_c(row[i0 - 1]) : C(0);
         vals[0] = left;
         #pragma unroll
         for (int k = 1; k < VEC; ++k) vals[k] = c[k - 1];
     } else {
-        C right = __shfl_down_sync(kFull, c[0], 1);
-        if (lane == 31) right = (i0 + VEC < nx) ? P::to_c(row[i0 + VEC]) : C(0);
+        C right = __shfl_down_sync(kFull, c[0], 1, seg);
+        if ((lane & (seg - 1)) == seg - 1) right = (loader && i0 + VEC < nx) ? P::to_c(row[i0 + VEC]) : C(0);
         #pragma unroll
         for (int k = 0; k < VEC - 1; ++k) vals[k] = c[k + 1];
         vals[VEC - 1] = right;
     }
 }
 
-template <int PREC, int VEC>
-__device__ __forceinline__ void store_vec(typename Prec<PREC>::R *p, const typename Prec<PREC>::C vals[VEC])
+template <class R, int VEC>
+__device__ __forceinline__ void store_vec(R *p, const R vals[VEC])
 {
-    using P = Prec<PREC>;
-    RVec<typename P::R, VEC> v;
+    RVec<R, VEC> v;
     #pragma unroll
-    for (int k = 0; k < VEC; ++k) v.v[k] = P::to_r(vals[k]);
-    *reinterpret_cast<RVec<typename P::R, VEC> *>(p) = v;
+    for (int k = 0; k < VEC; ++k) v.v[k] = vals[k];
+    *reinterpret_cast<RVec<R, VEC> *>(p) = v;
 }
 
-// row[i0 + k + s] = vals[k] for the VEC nodes of every active lane, s in {-1, 0, +1}.
-// Called by all 32 lanes of a warp (the shifted case exchanges values).  The
-// active lanes of a row form one contiguous range.  A shifted store is realigned
-// through the neighbour lane so that each lane writes its own aligned vector:
-// element c of that vector belongs to node c - s; an element whose node lies
-// in another warp is written by that node's own lane (the warp-edge store), and
-// an element whose node is not active is left alone.
-template <int PREC, int VEC>
-__device__ __forceinline__ void store_row(typename Prec<PREC>::R *row, int i0, int s, int lane, bool active,
-                                          const typename Prec<PREC>::C vals[VEC])
+// Warp shuffles of stored values (16-bit formats travel in a 32-bit register).
+template <class R>
+__device__ __forceinline__ R shfl_up_r(R v, int seg)
 {
-    using P = Prec<PREC>;
-    using C = typename P::C;
+    if constexpr (sizeof(R) == 2) return (R)__shfl_up_sync(kFull, (unsigned)v, 1, seg);
+    else return __shfl_up_sync(kFull, v, 1, seg);
+}
+template <class R>
+__device__ __forceinline__ R shfl_down_r(R v, int seg)
+{
+    if constexpr (sizeof(R) == 2) return (R)__shfl_down_sync(kFull, (unsigned)v, 1, seg);
+    else return __shfl_down_sync(kFull, v, 1, seg);
+}
+
+// Stores of `cnt` consecutive elements starting at row[c] (cnt <= 7 for 16-bit storage, where an
+// unaligned start is served by one 2-, 4- and 8-byte store each instead of cnt scalar stores).
+template <class R>
+__device__ __forceinline__ void store_run(R *row, int c, const R *v, int cnt)
+{
+    if constexpr (sizeof(R) == 2) {
+        int k = 0;
+        if ((c & 1) && k < cnt) { row[c] = v[k]; ++c; ++k; }
+        if ((c & 3) && cnt - k >= 2) {
+            *reinterpret_cast<unsigned *>(row + c) = (unsigned)v[k] | ((unsigned)v[k + 1] << 16);
+            c += 2; k += 2;
+        }
+        if (cnt - k >= 4) {
+            const unsigned lo = (unsigned)v[k] | ((unsigned)v[k + 1] << 16);
+            const unsigned hi = (unsigned)v[k + 2] | ((unsigned)v[k + 3] << 16);
+            *reinterpret_cast<uint2 *>(row + c) = make_uint2(lo, hi);
+            c += 4; k += 4;
+        }
+        if (cnt - k >= 2) {
+            *reinterpret_cast<unsigned *>(row + c) = (unsigned)v[k] | ((unsigned)v[k + 1] << 16);
+            c += 2; k += 2;
+        }
+        if (k < cnt) row[c] = v[k];
+    } else {
+        for (int k = 0; k < cnt; ++k) row[c + k] = v[k];
+    }
+}
+
+// row[i0 + k + s] = vals[k] (already in the storage format) for the VEC nodes of every active
+// lane, s in {-1, 0, +1}.  Called by all 32 lanes of a warp (the shifted case exchanges values).
+// The active lanes of a row segment form one contiguous range.  A shifted store is realigned
+// through the neighbour lane so that each lane writes its own aligned vector: element c of that
+// vector belongs to node c - s; an element whose node lies in another row segment is written by
+// that node's own lane (the segment-edge store), and an element whose node is not active is left
+// alone.
+template <class R, int VEC>
+__device__ __forceinline__ void store_row(R *row, int i0, int s, int lane, bool active, const R vals[VEC],
+                                          int seg = 32)
+{
     if (VEC == 1 || s == 0) {
         if (!active) return;
-        if (VEC == 1) row[i0 + s] = P::to_r(vals[0]);
-        else store_vec<PREC, VEC>(row + i0, vals);
+        if (VEC == 1) row[i0 + s] = vals[0];
+        else store_vec<R, VEC>(row + i0, vals);
         return;
     }
     if (s > 0) {
-        const C prev_last = __shfl_up_sync(kFull, vals[VEC - 1], 1);
-        const bool prev_active = (__shfl_up_sync(kFull, (int)active, 1) != 0) && lane != 0;
+        const R prev_last = shfl_up_r(vals[VEC - 1], seg);
+        const bool prev_active = (__shfl_up_sync(kFull, (int)active, 1, seg) != 0) && (lane & (seg - 1)) != 0;
         if (active && prev_active) {
-            C out[VEC];
+            R out[VEC];
             out[0] = prev_last;
             #pragma unroll
             for (int k = 1; k < VEC; ++k) out[k] = vals[k - 1];
-            store_vec<PREC, VEC>(row + i0, out);
+            store_vec<R, VEC>(row + i0, out);
         } else {
-            if (prev_active) row[i0] = P::to_r(prev_last);
-            if (active) {
-                #pragma unroll
-                for (int k = 1; k < VEC; ++k) row[i0 + k] = P::to_r(vals[k - 1]);
-            }
+            if (prev_active) row[i0] = prev_last;
+            if (active) store_run<R>(row, i0 + 1, vals, VEC - 1);
         }
-        if (active && lane == 31) row[i0 + VEC] = P::to_r(vals[VEC - 1]);
+        if (active && (lane & (seg - 1)) == seg - 1) row[i0 + VEC] = vals[VEC - 1];
     } else {
-        const C next_first = __shfl_down_sync(kFull, vals[0], 1);
-        const bool next_active = (__shfl_down_sync(kFull, (int)active, 1) != 0) && lane != 31;
+        const R next_first = shfl_down_r(vals[0], seg);
+        const bool next_active =
+            (__shfl_down_sync(kFull, (int)active, 1, seg) != 0) && (lane & (seg - 1)) != seg - 1;
         if (active && next_active) {
-            C out[VEC];
+            R out[VEC];
             #pragma unroll
             for (int k = 0; k < VEC - 1; ++k) out[k] = vals[k + 1];
             out[VEC - 1] = next_first;
-            store_vec<PREC, VEC>(row + i0, out);
+            store_vec<R, VEC>(row + i0, out);
         } else {
-            if (active) {
-                #pragma unroll
-                for (int k = 0; k < VEC - 1; ++k) row[i0 + k] = P::to_r(vals[k + 1]);
-            }
-            if (next_active) row[i0 + VEC - 1] = P::to_r(next_first);
+            if (active) store_run<R>(row, i0, vals + 1, VEC - 1);
+            if (next_active) row[i0 + VEC - 1] = next_first;
         }
-        if (active && lane == 0) row[i0 - 1] = P::to_r(vals[0]);
+        if (active && (lane & (seg - 1)) == 0) row[i0 - 1] = vals[0];
     }
+}
+
+// f*_a of node `node` in the storage format: rounded to nearest, or stochastically (SR) with the
+// bits of (node, a, the launch's step).
+template <int PREC, bool SR>
+__device__ __forceinline__ typename Prec<PREC>::R round_store(typename Prec<PREC>::C c, uint32_t node_hash, int a)
+{
+    if constexpr (SR) return Prec<PREC>::to_r_sr(c, sr_pop_bits(node_hash, a));
+    else return Prec<PREC>::to_r(c);
 }
 
 // One node through the full boundary resolution (band blocks, and the
 // reference behaviour every fast path must reproduce bit for bit).
-template <int PREC, int KIND, int MODE>
+template <int PREC, int KIND, int MODE, bool SR = false>
 __device__ __forceinline__ void step_node_generic(const typename Prec<PREC>::R *src,
                                                   typename Prec<PREC>::R *dst,
                                                   const Params<typename Prec<PREC>::C> &p, int i, int j)
@@ -183,17 +253,19 @@ __device__ __forceinline__ void step_node_generic(const typename Prec<PREC>::R *
         if (L.side >= 0) v += p.corr[L.side][a];
         g[a] = v;
     }
-    if (!collide<KIND>(p, g)) atomicOr(p.flag, 1);
+    if (!collide<KIND, Prec<PREC>::kExactWeights>(p, g)) atomicOr(p.flag, 1);
+    const uint32_t nh = SR ? sr_node_hash((uint32_t)j * (uint32_t)p.nx + (uint32_t)i, p.salt) : 0u;
     #pragma unroll
     for (int a = 0; a < 9; ++a) {
         Loc L = push_loc<MODE>(p, a, i, j);
-        dst[at(p.plane, p.pitch, L.plane, L.j, L.i)] = P::to_r(g[a]);
+        dst[at(p.plane, p.pitch, L.plane, L.j, L.i)] = round_store<PREC, SR>(g[a], nh, a);
     }
 }
 
 // Block b of one lattice's step grid (interior block or band block), executed
 // by all BX threads of the calling block.
-template <int PREC, int KIND, int MODE, int VEC, int BX, bool EDGE = true>
+// ROWSEG: the interior blocks follow the row-segmented geometry of step_geom_seg.
+template <int PREC, int KIND, int MODE, int VEC, int BX, bool EDGE = true, bool ROWSEG = false, bool SR = false>
 __device__ __forceinline__ void step_block(const typename Prec<PREC>::R *src, typename Prec<PREC>::R *dst,
                                            const Params<typename Prec<PREC>::C> &p, const StepGeom &geo, int b)
 {
@@ -216,16 +288,27 @@ __device__ __forceinline__ void step_block(const typename Prec<PREC>::R *src, ty
             int k = (int)(m % bw);
             i = k < geo.L ? k : geo.R + (k - geo.L);
         }
-        step_node_generic<PREC, KIND, MODE>(src, dst, p, i, j);
+        step_node_generic<PREC, KIND, MODE, SR>(src, dst, p, i, j);
         return;
     }
 
     // ---- interior: VEC nodes per thread, no boundary logic ----
     const int lane = tid & 31;
-    const int j = 1 + b / geo.bpr;
-    const int i0 = (b % geo.bpr) * (BX * VEC) + tid * VEC;
-    const bool active = (i0 >= geo.L) && (i0 + VEC <= geo.R);
-    const bool loader = (VEC == 1) ? active : (i0 < p.nx);
+    int j, i0, seg = 32;
+    bool valid = true;
+    if (ROWSEG) {
+        seg = 1 << geo.seg_log2;
+        const int task = b * (BX >> geo.seg_log2) + (tid >> geo.seg_log2);
+        valid = task < geo.tasks;
+        const int tk = valid ? task : 0;
+        j = 1 + tk / geo.spr;
+        i0 = ((tk % geo.spr) << geo.seg_log2) * VEC + (tid & (seg - 1)) * VEC;
+    } else {
+        j = 1 + b / geo.bpr;
+        i0 = (b % geo.bpr) * (BX * VEC) + tid * VEC;
+    }
+    const bool active = valid && (i0 >= geo.L) && (i0 + VEC <= geo.R);
+    const bool loader = (VEC == 1) ? active : (valid && i0 < p.nx);
 
     C g[VEC][9];
     #pragma unroll
@@ -235,7 +318,7 @@ __device__ __forceinline__ void step_block(const typename Prec<PREC>::R *src, ty
         const int s = (MODE == MODE_AA_EVEN) ? 0 : -ex(a);
         const typename Prec<PREC>::R *rp = src + (size_t)plane * (size_t)p.plane + (size_t)row * (size_t)p.pitch;
         C vals[VEC];
-        load_row<PREC, VEC>(rp, i0, s, lane, loader, p.nx, vals);
+        load_row<PREC, VEC>(rp, i0, s, lane, loader, p.nx, vals, seg);
         #pragma unroll
         for (int k = 0; k < VEC; ++k) g[k][a] = vals[k];
     }
@@ -266,29 +349,34 @@ __device__ __forceinline__ void step_block(const typename Prec<PREC>::R *src, ty
     }
     bool ok = true;
     #pragma unroll
-    for (int k = 0; k < VEC; ++k) ok &= collide<KIND>(p, g[k]);
+    for (int k = 0; k < VEC; ++k) ok &= collide<KIND, Prec<PREC>::kExactWeights>(p, g[k]);
     // only the in-place odd step exchanges values between lanes when storing
     if (!active && !(MODE == MODE_AA_ODD && VEC > 1)) return;
     if (active && !ok) atomicOr(p.flag, 1);
+    using R = typename Prec<PREC>::R;
+    uint32_t nh[VEC];
+    #pragma unroll
+    for (int k = 0; k < VEC; ++k)
+        nh[k] = SR ? sr_node_hash((uint32_t)j * (uint32_t)p.nx + (uint32_t)(i0 + k), p.salt) : 0u;
     #pragma unroll
     for (int a = 0; a < 9; ++a) {
         const int plane = (MODE == MODE_AA_EVEN) ? opp(a) : a;
         const int row = (MODE == MODE_AA_ODD) ? j + ey(a) : j;
         const int s = (MODE == MODE_AA_ODD) ? ex(a) : 0;
-        typename Prec<PREC>::R *rp = dst + (size_t)plane * (size_t)p.plane + (size_t)row * (size_t)p.pitch;
-        C vals[VEC];
+        R *rp = dst + (size_t)plane * (size_t)p.plane + (size_t)row * (size_t)p.pitch;
+        R vals[VEC];
         #pragma unroll
-        for (int k = 0; k < VEC; ++k) vals[k] = g[k][a];
-        store_row<PREC, VEC>(rp, i0, s, lane, active, vals);
+        for (int k = 0; k < VEC; ++k) vals[k] = round_store<PREC, SR>(g[k][a], nh[k], a);
+        store_row<R, VEC>(rp, i0, s, lane, active, vals, seg);
     }
 }
 
-template <int PREC, int KIND, int MODE, int VEC, int BX>
+template <int PREC, int KIND, int MODE, int VEC, int BX, bool SR = false>
 __global__ void __launch_bounds__(BX)
 step_kernel(const typename Prec<PREC>::R *src, typename Prec<PREC>::R *dst,
             const Params<typename Prec<PREC>::C> p, const StepGeom geo)
 {
-    step_block<PREC, KIND, MODE, VEC, BX>(src, dst, p, geo, blockIdx.x);
+    step_block<PREC, KIND, MODE, VEC, BX, true, false, SR>(src, dst, p, geo, blockIdx.x);
 }
 
 // ---- state I/O and macros (one thread per node of a row chunk) -------------------
@@ -341,8 +429,24 @@ __global__ void set_f_kernel(typename Prec<PREC>::R *state, const double *f, int
     }
 }
 
+// One population of f^eq(rho, u) (Eq. feq-full) as an offset, stored through the pull map.
+// Float arithmetic for the 32- and 16-bit formats (their stored value has at most 24
+// significant bits); the weight product is rounded as for an exact weight.
+template <int PREC, int MODE, int A>
+__device__ __forceinline__ void init_store_f(typename Prec<PREC>::R *state, const Params<float> &p, int i, int j,
+                                             float drho, float d, float ux, float uy, float uu)
+{
+    using P = Prec<PREC>;
+    const float eu = float(ex(A)) * ux + float(ey(A)) * uy;
+    float g = WeightMul<float>::template mul<A>(drho + d * (3.0f * eu + 4.5f * eu * eu - 1.5f * uu));
+    const Loc L = pull_loc<MODE>(p, A, i, j);
+    if (L.side >= 0) g -= p.corr[L.side][A];
+    state[at(p.plane, p.pitch, L.plane, L.j, L.i)] = P::to_r(g);
+}
+
 // f = f^eq(rho, u) (Eq. feq-full), written as offsets through the pull map;
-// rho == NULL selects rho = 1, u = 0.
+// rho == NULL selects rho = 1, u = 0.  rho and u may be device memory or host memory
+// the device can address (page-locked and mapped).
 template <int PREC, int MODE>
 __global__ void init_macros_kernel(typename Prec<PREC>::R *state, const double *rho, const double *u,
                                    int row0, int rows, const Params<typename Prec<PREC>::C> p)
@@ -359,14 +463,28 @@ __global__ void init_macros_kernel(typename Prec<PREC>::R *state, const double *
         ux = u[q];
         uy = u[(size_t)rows * p.nx + q];
     }
-    double uu = ux * ux + uy * uy;
-    #pragma unroll
-    for (int a = 0; a < 9; ++a) {
-        double eu = ex(a) * ux + ey(a) * uy;
-        double g = wgt<double>(a) * ((d - 1.0) + d * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu));
-        Loc L = pull_loc<MODE>(p, a, i, j);
-        if (L.side >= 0) g -= (double)p.corr[L.side][a];
-        state[at(p.plane, p.pitch, L.plane, L.j, L.i)] = P::to_r((typename P::C)g);
+    if constexpr (PREC == SMRT_PREC_F64) {
+        double uu = ux * ux + uy * uy;
+        #pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            double eu = ex(a) * ux + ey(a) * uy;
+            double g = wgt<double>(a) * ((d - 1.0) + d * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu));
+            Loc L = pull_loc<MODE>(p, a, i, j);
+            if (L.side >= 0) g -= (double)p.corr[L.side][a];
+            state[at(p.plane, p.pitch, L.plane, L.j, L.i)] = P::to_r((typename P::C)g);
+        }
+    } else {
+        const float drho = (float)(d - 1.0), df = (float)d, fx = (float)ux, fy = (float)uy;
+        const float uu = fx * fx + fy * fy;
+        init_store_f<PREC, MODE, 0>(state, p, i, j, drho, df, fx, fy, uu);
+        init_store_f<PREC, MODE, 1>(state, p, i, j, drho, df, fx, fy, uu);
+        init_store_f<PREC, MODE, 2>(state, p, i, j, drho, df, fx, fy, uu);
+        init_store_f<PREC, MODE, 3>(state, p, i, j, drho, df, fx, fy, uu);
+        init_store_f<PREC, MODE, 4>(state, p, i, j, drho, df, fx, fy, uu);
+        init_store_f<PREC, MODE, 5>(state, p, i, j, drho, df, fx, fy, uu);
+        init_store_f<PREC, MODE, 6>(state, p, i, j, drho, df, fx, fy, uu);
+        init_store_f<PREC, MODE, 7>(state, p, i, j, drho, df, fx, fy, uu);
+        init_store_f<PREC, MODE, 8>(state, p, i, j, drho, df, fx, fy, uu);
     }
 }
 
@@ -385,6 +503,59 @@ __device__ __forceinline__ void moments_d(const double g[9], double &rho, double
     uy = jy / rho;
 }
 
+// s + c += x without rounding error in s + c (Knuth's two-sum; c collects the error terms).
+__device__ __forceinline__ void two_sum_acc(float &s, float &c, float x)
+{
+    const float t = s + x;
+    const float bp = t - s;
+    c += (s - (t - bp)) + (x - bp);
+    s = t;
+}
+
+// The moments of Eq. (fea-0) of nine float offsets, in double, with few double operations:
+// each sum is formed in float as an unevaluated pair hi + lo (two-sum), which carries about
+// 48 significant bits of it, and 1 / rho is the float reciprocal refined by two Newton steps
+// (to double rounding).  The double pipe is the scarce unit of this GPU; this form needs about
+// a quarter of the double operations of moments_d, whose results it matches to ~1e-14.
+__device__ __forceinline__ void moments_f(const float g[9], double &rho, double &ux, double &uy)
+{
+    float s0 = g[0], c0 = 0.0f, sx = g[1], cx = 0.0f, sy = g[2], cy = 0.0f;
+    two_sum_acc(s0, c0, g[1]);
+    two_sum_acc(s0, c0, g[2]);
+    two_sum_acc(s0, c0, g[3]);
+    two_sum_acc(s0, c0, g[4]);
+    two_sum_acc(s0, c0, g[5]);
+    two_sum_acc(s0, c0, g[6]);
+    two_sum_acc(s0, c0, g[7]);
+    two_sum_acc(s0, c0, g[8]);
+    two_sum_acc(sx, cx, -g[3]);
+    two_sum_acc(sx, cx, g[5]);
+    two_sum_acc(sx, cx, -g[6]);
+    two_sum_acc(sx, cx, -g[7]);
+    two_sum_acc(sx, cx, g[8]);
+    two_sum_acc(sy, cy, -g[4]);
+    two_sum_acc(sy, cy, g[5]);
+    two_sum_acc(sy, cy, g[6]);
+    two_sum_acc(sy, cy, -g[7]);
+    two_sum_acc(sy, cy, -g[8]);
+    rho = 1.0 + ((double)s0 + (double)c0);
+    const double r0 = (double)(1.0f / (float)rho);
+    const double r1 = r0 * (2.0 - rho * r0);
+    const double inv = r1 * (2.0 - rho * r1);
+    ux = ((double)sx + (double)cx) * inv;
+    uy = ((double)sy + (double)cy) * inv;
+}
+
+// moments_d for double offsets, moments_f for float ones.
+__device__ __forceinline__ void moments_any(const double g[9], double &rho, double &ux, double &uy)
+{
+    moments_d(g, rho, ux, uy);
+}
+__device__ __forceinline__ void moments_any(const float g[9], double &rho, double &ux, double &uy)
+{
+    moments_f(g, rho, ux, uy);
+}
+
 template <int PREC, int MODE>
 __global__ void macros_kernel(const typename Prec<PREC>::R *state, double *rho, double *u, int row0,
                               int rows, const Params<typename Prec<PREC>::C> p)
@@ -395,11 +566,8 @@ __global__ void macros_kernel(const typename Prec<PREC>::R *state, double *rho, 
     int r = (int)(t / p.nx), i = (int)(t % p.nx);
     typename Prec<PREC>::C g[9];
     pull_canonical<PREC, MODE>(state, p, i, row0 + r, g);
-    double gd[9];
-    #pragma unroll
-    for (int a = 0; a < 9; ++a) gd[a] = (double)g[a];
     double rr, ux, uy;
-    moments_d(gd, rr, ux, uy);
+    moments_any(g, rr, ux, uy);
     size_t q = (size_t)r * p.nx + i;
     if (rho) rho[q] = rr;
     if (u) {
@@ -422,7 +590,7 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-template <int PREC, int KIND, int MODE>
+template <int PREC, int KIND, int MODE, bool SR = false>
 __global__ void __launch_bounds__(256)
 residual_kernel(const typename Prec<PREC>::R *state, const Params<typename Prec<PREC>::C> p,
                 double *partials, int tiles_x, int tiles_y)
@@ -447,34 +615,31 @@ residual_kernel(const typename Prec<PREC>::R *state, const Params<typename Prec<
             C g[9];
             pull_canonical<PREC, MODE>(state, p, i, j, g);
             if (tile_node) {
-                double gd[9], rr, ux, uy;
-                #pragma unroll
-                for (int a = 0; a < 9; ++a) gd[a] = (double)g[a];
-                moments_d(gd, rr, ux, uy);
+                double rr, ux, uy;
+                moments_any(g, rr, ux, uy);
                 u0s[0][hy - 1][hx - 1] = rr;
                 u0s[1][hy - 1][hx - 1] = ux;
                 u0s[2][hy - 1][hx - 1] = uy;
             }
-            collide<KIND>(p, g);
+            collide<KIND, Prec<PREC>::kExactWeights>(p, g);
+            const uint32_t nh = SR ? sr_node_hash((uint32_t)j * (uint32_t)p.nx + (uint32_t)i, p.salt) : 0u;
             #pragma unroll
-            for (int a = 0; a < 9; ++a) post[a][hy][hx] = P::to_r(g[a]);
+            for (int a = 0; a < 9; ++a) post[a][hy][hx] = round_store<PREC, SR>(g[a], nh, a);
         }
         __syncthreads();
         const int lx = tid % kRTX, ly = tid / kRTX;
         const int i = tx0 + lx, j = ty0 + ly;
         if (i < p.nx && j < p.ny) {
-            double g1[9];
+            C g1[9];
             #pragma unroll
             for (int a = 0; a < 9; ++a) {
                 int si = i - ex(a), sj = j - ey(a);
                 int side = resolve(p, si, sj);
-                C v;
-                if (side >= 0) v = P::to_c(post[opp(a)][ly + 1][lx + 1]) + p.corr[side][a];
-                else v = P::to_c(post[a][ly + 1 - ey(a)][lx + 1 - ex(a)]);
-                g1[a] = (double)v;
+                if (side >= 0) g1[a] = P::to_c(post[opp(a)][ly + 1][lx + 1]) + p.corr[side][a];
+                else g1[a] = P::to_c(post[a][ly + 1 - ey(a)][lx + 1 - ex(a)]);
             }
             double r1, ux1, uy1;
-            moments_d(g1, r1, ux1, uy1);
+            moments_any(g1, r1, ux1, uy1);
             const double r0 = u0s[0][ly][lx], ux0 = u0s[1][ly][lx], uy0 = u0s[2][ly][lx];
             const double dx = ux1 - ux0, dy = uy1 - uy0;
             acc[0] += dx * dx + dy * dy;
@@ -559,6 +724,13 @@ cudaError_t launch_step_km(const void *src, void *dst, const HostParams &hp, cud
     const long long blocks = (long long)geo.n_int_blocks + edge_blocks;
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    if constexpr (PREC == SMRT_PREC_F16 || PREC == SMRT_PREC_BF16) {
+        if (hp.rounding == SMRT_ROUND_STOCHASTIC) {
+            step_kernel<PREC, KIND, MODE, VEC, BX, true><<<(unsigned)blocks, BX, 0, s>>>(
+                (const R *)src, (R *)dst, p, geo);
+            return cudaGetLastError();
+        }
+    }
     step_kernel<PREC, KIND, MODE, VEC, BX><<<(unsigned)blocks, BX, 0, s>>>(
         (const R *)src, (R *)dst, p, geo);
     return cudaGetLastError();
@@ -657,8 +829,18 @@ cudaError_t launch_residual_k(int mode, const void *state, const HostParams &hp,
     const int tiles_x = (hp.nx + kRTX - 1) / kRTX, tiles_y = (hp.ny + kRTY - 1) / kRTY;
     long long nt = (long long)tiles_x * tiles_y;
     const int nb = (int)(nt < kResidualMaxBlocks ? nt : kResidualMaxBlocks);
-    SMRT_MODE_SWITCH(mode, (residual_kernel<PREC, KIND, M><<<nb, 256, 0, s>>>((const typename P::R *)state, p,
-                                                                                 sc.partials, tiles_x, tiles_y)));
+    bool plain = true;
+    if constexpr (PREC == SMRT_PREC_F16 || PREC == SMRT_PREC_BF16) {
+        if (hp.rounding == SMRT_ROUND_STOCHASTIC) {
+            plain = false;
+            SMRT_MODE_SWITCH(mode, (residual_kernel<PREC, KIND, M, true><<<nb, 256, 0, s>>>(
+                                       (const typename P::R *)state, p, sc.partials, tiles_x, tiles_y)));
+        }
+    }
+    if (plain) {
+        SMRT_MODE_SWITCH(mode, (residual_kernel<PREC, KIND, M><<<nb, 256, 0, s>>>((const typename P::R *)state, p,
+                                                                                     sc.partials, tiles_x, tiles_y)));
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     reduce_partials_kernel<<<1, 256, 0, s>>>(sc.partials, nb, sc.sums);

@@ -69,9 +69,12 @@ def test_options_before_first_use():
     S.smrt_set_option(h, S.SMRT_OPT_MEM_LIMIT, 1 << 20)
     assert S.smrt_get_option(h, S.SMRT_OPT_PRECISION) == S.SMRT_PREC_F32
     assert S.smrt_get_option(h, S.SMRT_OPT_TAU_S) == 0.9
+    assert S.smrt_get_option(h, S.SMRT_OPT_ROUNDING) == S.SMRT_ROUND_NEAREST
+    S.smrt_set_option(h, S.SMRT_OPT_ROUNDING, S.SMRT_ROUND_STOCHASTIC)
+    assert S.smrt_get_option(h, S.SMRT_OPT_ROUNDING) == S.SMRT_ROUND_STOCHASTIC
     for key, val in [(S.SMRT_OPT_TAU_S, 0.5), (S.SMRT_OPT_TAU, -1.0), (S.SMRT_OPT_COLLISION, 7),
                      (S.SMRT_OPT_LAYOUT, 2), (S.SMRT_OPT_PRECISION, 9), (S.SMRT_OPT_CHECK_DIVERGENCE, 0.5),
-                     (999, 0.0)]:
+                     (S.SMRT_OPT_ROUNDING, 2), (S.SMRT_OPT_ROUNDING, 0.5), (999, 0.0)]:
         with pytest.raises(S.SmrtError) as ei:
             S.smrt_set_option(h, key, val)
         assert ei.value.status == S.SMRT_ERR_ARG

@@ -19,8 +19,10 @@ def test_round_trip_is_exact(tmp_path):
     C.write_checkpoint(p, _header(), f)
     assert os.path.getsize(p) == 96 + 9 * 5 * 7 * 8
     hdr, g = C.read_checkpoint(p)
-    assert hdr == _header()
+    assert hdr == dict(_header(), rounding=0)         # written without a rounding field: nearest
     assert np.array_equal(f, g)
+    C.write_checkpoint(p, dict(_header(), rounding=1), f)
+    assert C.read_checkpoint(p)[0]["rounding"] == 1
 
 
 def test_rejects_other_files(tmp_path):
