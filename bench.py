@@ -39,7 +39,8 @@ def parse_args(argv=None):
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", choices=["tgv8192", "cavity4096"], default="tgv8192")
     p.add_argument("--layout", choices=["ab", "aa"], default="ab")
-    p.add_argument("--prec", choices=["f32", "f16", "bf16", "f64"], default="f32")
+    p.add_argument("--prec", choices=["f32", "f16", "bf16", "f64", "f16-sr", "bf16-sr"], default="f32",
+                   help="storage precision; -sr: 16-bit storage with stochastic rounding")
     p.add_argument("--kind", choices=["smrt", "srt"], default="smrt")
     p.add_argument("--variant-steps", type=int, default=2000,
                    help="steps per extra variant line (0 disables the variants)")
@@ -51,6 +52,8 @@ def parse_args(argv=None):
                    default="",
                    help="precision: 16-bit vs FP32 storage report; batched: 512 cavities to steady state "
                         "(each prints its own JSON line)")
+    p.add_argument("--no-learned", action="store_true",
+                   help="leave the learned warm-start leg (training + time to steady at the same error) out")
     p.add_argument("--learned-count", type=int, default=2000)
     p.add_argument("--learned-iters", type=int, default=2000)
     p.add_argument("--learned-cap", type=int, default=150000)
@@ -227,7 +230,11 @@ def committed_traffic(prec, layout, kind):
 # ---- the GPU arm ---------------------------------------------------------------------
 
 def make_handle(S, wl, prec, layout, kind, check=True):
+    """prec: f64, f32, f16 or bf16, with "-sr" for stochastic rounding of the 16-bit formats."""
     h = S.smrt_create(wl["nx"], wl["ny"], wl["tau"], wl["u_lid"], wl["bc"])
+    if prec.endswith("-sr"):
+        prec = prec[:-3]
+        S.smrt_set_option(h, S.SMRT_OPT_ROUNDING, S.SMRT_ROUND_STOCHASTIC)
     S.smrt_set_option(h, S.SMRT_OPT_PRECISION, {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}[prec])
     S.smrt_set_option(h, S.SMRT_OPT_LAYOUT, {"ab": 0, "aa": 1}[layout])
     S.smrt_set_option(h, S.SMRT_OPT_COLLISION, {"smrt": 0, "srt": 1}[kind])
@@ -259,18 +266,64 @@ def run_variant(S, wl, rho_d, u_d, prec, layout, kind, steps, warmup, world):
     nodes = wl["nx"] * wl["ny"]
     mlups = nodes * steps / (ms * 1e-3) / 1e6
     return {"mlups": round(mlups, 1), "ms_per_step": round(ms / steps, 5),
-            "hbm_gbs": round(BYTES_PER_NODE[prec] * nodes / (ms / steps * 1e-3) / 1e9, 1), "steps": steps}
+            "hbm_gbs": round(BYTES_PER_NODE[prec.replace("-sr", "")] * nodes / (ms / steps * 1e-3) / 1e9, 1),
+            "steps": steps}
 
 
-def e2e_run(S, wl, prec, layout, kind, steps, world):
+def host_link_gbs(host, reps=3):
+    """Pinned host <-> device copy bandwidth (GB/s, best of reps, CUDA events) for a pinned tensor."""
+    import torch
+    dev = torch.empty(host.shape, dtype=host.dtype, device="cuda")
+    best = {"h2d": 0.0, "d2h": 0.0}
+    for _ in range(reps):
+        for name, (dst, src) in (("h2d", (dev, host)), ("d2h", (host, dev))):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            dst.copy_(src, non_blocking=True)
+            b.record()
+            torch.cuda.synchronize()
+            best[name] = max(best[name], host.numel() * host.element_size() / (a.elapsed_time(b) * 1e-3) / 1e9)
+    del dev
+    return best
+
+
+def precision_errors(S, n=1024, re=5000.0, steps=20000, U=0.1):
+    """Velocity error of each storage format against the FP64 path after `steps` updates of an n^2
+    cavity (SmrtLBM, two-buffer layout): max and rms over nodes of |u - u_FP64| / U_lid.  The FP64
+    path itself matches the FP64 CPU oracle to <= 1e-12 (parity tests)."""
+    import torch
+    from paper_2409_01076_gb300 import workloads as W
+    wl = dict(nx=n, ny=n, tau=W.cavity_tau(n, U, re), u_lid=U, bc=W.CAVITY)
+    us = {}
+    for prec in ("f64", "f32", "f16", "bf16", "f16-sr", "bf16-sr"):
+        h = make_handle(S, wl, prec, "ab", "smrt", check=False)
+        S.smrt_step(h, steps)
+        rho = torch.empty((n, n), dtype=torch.float64, device="cuda")
+        u = torch.empty((2, n, n), dtype=torch.float64, device="cuda")
+        S.smrt_macros(h, rho, u)
+        S.smrt_destroy(h)
+        us[prec] = u
+    out = {"lattice": "lid-driven cavity %dx%d, Re %g, U_lid %g, tau %.5f" % (n, n, re, U, wl["tau"]),
+           "steps": steps, "reference": "FP64 storage and arithmetic (same kernels)", "unit": "|du| / U_lid",
+           "note": "-sr: stochastic rounding of the stored 16-bit offsets (SMRT_ROUND_STOCHASTIC)"}
+    for prec in ("f32", "f16", "bf16", "f16-sr", "bf16-sr"):
+        d = us[prec] - us["f64"]
+        out[prec] = {"max": float(d.abs().amax()) / U, "rms": float((d * d).sum(0).mean().sqrt()) / U}
+    return out
+
+
+def e2e_run(S, wl, prec, layout, kind, steps, world, ms_per_step=None):
     """Same metric through the public C ABI with host buffers: pinned host (rho, u)
-    in, K updates, pinned host (rho, u) out, all inside the timed region."""
+    in, K updates, pinned host (rho, u) out, all inside the timed region.  The
+    library's kernels read and write the pinned buffers directly over the host link."""
     import torch
     rho, u = initial_fields(wl)
     rho_h = torch.from_numpy(rho).pin_memory()
     u_h = torch.from_numpy(u).pin_memory()
     rho_o = torch.empty_like(rho_h).pin_memory()
     u_o = torch.empty_like(u_h).pin_memory()
+    link = host_link_gbs(u_h)
     h = make_handle(S, wl, prec, layout, kind)
     S.smrt_step(h, 1)                      # allocate the state outside the timed region
     S.smrt_macros(h, rho_o, u_o)           # and the staging buffer
@@ -288,10 +341,17 @@ def e2e_run(S, wl, prec, layout, kind, steps, world):
     h2d = rho_h.numel() * 8 + u_h.numel() * 8
     d2h = rho_o.numel() * 8 + u_o.numel() * 8
     finite = bool(torch.isfinite(u_o).all())
-    return {"value": round(world * nodes * steps / sec / 1e6, 1), "unit": "MLUPS",
-            "h2d_bytes_per_step": round(h2d / steps, 1), "d2h_bytes_per_step": round(d2h / steps, 1),
-            "h2d_bytes_total": h2d, "d2h_bytes_total": d2h, "seconds": round(sec, 4), "steps": steps,
-            "api": "smrt_init_macros(host) + smrt_step(K) + smrt_macros(host)", "result_finite": finite}
+    out = {"value": round(world * nodes * steps / sec / 1e6, 1), "unit": "MLUPS",
+           "h2d_bytes_per_step": round(h2d / steps, 1), "d2h_bytes_per_step": round(d2h / steps, 1),
+           "h2d_bytes_total": h2d, "d2h_bytes_total": d2h, "seconds": round(sec, 4), "steps": steps,
+           "api": "smrt_init_macros(host) + smrt_step(K) + smrt_macros(host)", "result_finite": finite,
+           "host_link_gbs": {k: round(v, 1) for k, v in link.items()},
+           "host_buffers": "page-locked (pinned torch tensors), read and written by the kernels over the host link"}
+    if ms_per_step:
+        bound = h2d / (link["h2d"] * 1e9) + d2h / (link["d2h"] * 1e9) + steps * ms_per_step * 1e-3
+        out["link_bound_seconds"] = round(bound, 4)
+        out["frac_of_link_bound"] = round(bound / sec, 3)
+    return out
 
 
 # ---- the CPU oracle (baseline / reference arm) ------------------------------------------------
@@ -460,7 +520,7 @@ def gpu_arm(args):
     mlups = world * nodes * args.steps / sec / 1e6
     per_launch = sec / args.steps
     peak, peak_src = measured_hbm_peak()
-    achieved = BYTES_PER_NODE[args.prec] * nodes / per_launch / 1e9
+    achieved = BYTES_PER_NODE[args.prec.replace("-sr", "")] * nodes / per_launch / 1e9
     traffic_per_node, _ = committed_traffic(args.prec, args.layout, args.kind)
 
     result = {
@@ -471,13 +531,13 @@ def gpu_arm(args):
         "config": {"workload": wl["desc"], "nodes": nodes, "storage": "%s offsets f - w" % args.prec,
                    "layout": args.layout, "collision": args.kind,
                    "l2": "no flush: populations (%.2f GB) exceed the 129 MB L2"
-                         % (BYTES_PER_NODE[args.prec] / 2 * nodes * (2 if args.layout == "ab" else 1) / 1e9),
+                         % (BYTES_PER_NODE[args.prec.replace("-sr", "")] / 2 * nodes * (2 if args.layout == "ab" else 1) / 1e9),
                    "parallelism": "replicas x%d" % world},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src
                      if peak_src == "measured" else "fallback 6.8 TB/s",
                      "traffic": (round(traffic_per_node * nodes) if traffic_per_node else None),
-                     "algorithmic_bytes_per_launch": BYTES_PER_NODE[args.prec] * nodes,
+                     "algorithmic_bytes_per_launch": BYTES_PER_NODE[args.prec.replace("-sr", "")] * nodes,
                      "kernel": "step_kernel<%s,%s,%s>" % (args.prec, args.kind, args.layout)},
         "gpu_launches": args.steps,
         "clocks": clk,
@@ -488,7 +548,8 @@ def gpu_arm(args):
         variants = {}
         vs = args.variant_steps
         for prec, layout, kind in [("f32", "ab", "srt"), ("f32", "aa", "smrt"), ("f32", "aa", "srt"),
-                                   ("f16", "ab", "smrt"), ("bf16", "ab", "smrt"), ("f16", "aa", "smrt")]:
+                                   ("f16", "ab", "smrt"), ("bf16", "ab", "smrt"), ("f16", "aa", "smrt"),
+                                   ("f16-sr", "ab", "smrt"), ("bf16-sr", "ab", "smrt"), ("f16-sr", "aa", "smrt")]:
             if (prec, layout, kind) == (args.prec, args.layout, args.kind):
                 continue
             variants["%s-%s-%s" % (prec, layout, kind)] = run_variant(S, wl, rho_d, u_d, prec, layout, kind, vs,
@@ -500,15 +561,19 @@ def gpu_arm(args):
                     S, cav, None, None, "f32", layout, kind, vs, 10, world)
             variants["batched512-f32-ab-smrt"] = batched_throughput(S, max(vs // 10, 20))
         result["variants"] = variants
+        if rank == 0:
+            result["precision_error"] = precision_errors(S)
 
     del rho_d, u_d
     torch.cuda.empty_cache()
     if not args.no_e2e:
-        result["e2e"] = e2e_run(S, wl, args.prec, args.layout, args.kind, args.steps, world)
+        result["e2e"] = e2e_run(S, wl, args.prec, args.layout, args.kind, args.steps, world, ms / args.steps)
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(wl)
     elif not args.no_cpu:
         result["cpu_baseline"] = None
+    if rank == 0 and world == 1 and not args.no_learned:
+        result["learned"] = learned_leg(args)
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
@@ -659,42 +724,71 @@ def paper_experiments_report(args):
     return 0
 
 
-def learned_report(args):
-    """U-Net warm start: solver-generated steady 256^2 cavities (Re log-uniform in [100, 1e4]), training on
-    the GPU with libsmrt's NN kernels, then time-to-steady (stride residual 1e-7) cold vs warm on held-out Re
-    at 256^2 and 1024^2."""
+def _geomean(xs):
     import numpy as np
+    xs = [x for x in xs if x]
+    return float(np.exp(np.mean(np.log(xs)))) if xs else None
+
+
+def learned_leg(args, held_out=((256, "f64", (130.0, 400.0, 1200.0, 2500.0), 400000, (1e-3,)),
+                                (1024, "f32", (130.0, 400.0, 1200.0), 1200000, (1e-3,)))):
+    """The learned warm start of the 256^2 cavity workload, trained in this run: 2,000 solver-generated
+    steady cavities (Re log-uniform in [100, 1e4]), U-Net training on the GPU, then time to steady state
+    at the same error, cold vs warm, on held-out Re (warmstart.time_to_same_error): 256^2 in FP64 and
+    1024^2 in FP32, each at the plain method's own error at its criterion and at 1e-3 U."""
     import torch
     import paper_2409_01076_gb300 as S
     from paper_2409_01076_gb300 import warmstart as WS
     from paper_2409_01076_gb300.unet import UNet
-    torch.cuda.set_device(0)
-    S._lib.load()
-    out = {"report": "learned", "U_lid": WS.U_LID, "tol": args.tol, "residual": "stride"}
+    t0 = time.perf_counter()
     res_train = WS.sample_res(args.learned_count, seed=1)
     targets, info = WS.generate_dataset(res_train, 256, args.tol, 1000, args.learned_cap)
-    out["dataset"] = info
     net = UNet(base=32, seed=0)
-    out["params"] = net.n_params()
     hist, train_s = WS.train(net, res_train, targets, iters=args.learned_iters, batch=16, lr=1e-3, warmup=100)
-    out["training"] = {"iters": args.learned_iters, "batch": 16, "lr": 1e-3, "warmup": 100,
-                       "seconds": round(train_s, 2),
-                       "loss_first_last": [hist[0][1], hist[-1][1]], "loss_history": hist[::4],
-                       "final_loss_scale": net.grad_scale}
     del targets
     torch.cuda.empty_cache()
-    held_out = [130.0, 400.0, 1200.0, 3500.0, 8000.0]
-    out["held_out_re"] = held_out
-    for n, cap in ((256, args.learned_cap * 2), (1024, args.learned_cap_1024)):
-        cold, fc = WS.time_to_steady(held_out, n, None, args.tol, 1000, cap)
-        warm, fw = WS.time_to_steady(held_out, n, net, args.tol, 1000, cap)
-        diff = [float((a - b).abs().max().item() / WS.U_LID) for a, b in zip(fc, fw)]
-        both = [k for k in range(len(held_out)) if cold["state"][k] == 1 and warm["state"][k] == 1]
-        factors = [cold["steps"][k] / warm["steps"][k] for k in both]
-        out["n%d" % n] = {"cold": cold, "warm": warm, "final_field_max_diff_over_U": diff,
-                          "steps_factor_converged": factors,
-                          "steps_factor_geomean": float(np.exp(np.mean(np.log(factors)))) if factors else None,
-                          "wall_factor": cold["wall_s"] / warm["wall_s"]}
+    out = {"workload": "U-Net (4 levels, 32 base channels, half operands / float32 accumulation) trained on "
+                       "%d solver-generated 256^2 cavities, U_lid 0.1, Re log-uniform in [100, 1e4]"
+                       % args.learned_count,
+           "dataset": info, "params": net.n_params(),
+           "training": {"iters": args.learned_iters, "batch": 16, "lr": 1e-3, "seconds": round(train_s, 2),
+                        "loss_first_last": [hist[0][1], hist[-1][1]]},
+           "error_definition": "each run (cold from rest, warm from the prediction) is continued past the plain "
+                               "method's criterion (stride residual < %g) until its residual < 1e-11 or 4x (FP64) "
+                               "/ 3x (FP32) the criterion's steps: its own converged field u_inf; "
+                               "e(t) = max over nodes |u(t) - u_inf| / U_lid; same error = the cold run's e at "
+                               "its criterion; the warm run's steps are those until its e falls to that; "
+                               "final_diff = max |u_inf,warm - u_inf,cold| / U_lid (the steady state depends on "
+                               "the start: halfway bounce-back leaves it non-unique)" % args.tol,
+           "residual": "stride: ||u(t) - u(t-K)|| / (K ||u(t)||), K = 1000", "cases": []}
+    for n, prec, res, cap, levels in held_out:
+        p = {"f64": S.SMRT_PREC_F64, "f32": S.SMRT_PREC_F32}[prec]
+        rows = WS.time_to_same_error(net, res, n, p, args.tol, 1e-11, levels, 1000, cap,
+                                     ref_factor=4 if prec == "f64" else 3)
+        out["cases"].extend(rows)
+        summary = {"precision": prec, "cavities": len(rows)}
+        for name in ["same_error"] + ["level_%g" % lv for lv in levels]:
+            done = [r["targets"][name] for r in rows if not r["capped"] and "steps_factor" in r["targets"][name]]
+            summary[name] = {"steps_factor_geomean": _geomean([t["steps_factor"] for t in done]),
+                             "wall_factor_geomean": _geomean([t["wall_factor"] for t in done]),
+                             "compared": len(done)}
+        out["n%d_%s" % (n, prec)] = summary
+    out["seconds"] = round(time.perf_counter() - t0, 1)
+    return out
+
+
+def learned_report(args):
+    """The learned leg of the default line on the full held-out set (256^2 and 1024^2 at Re 130, 400,
+    1,200, 3,500 and 8,000), printed as its own JSON line."""
+    import torch
+    import paper_2409_01076_gb300 as S
+    torch.cuda.set_device(0)
+    S._lib.load()
+    full = (130.0, 400.0, 1200.0, 3500.0, 8000.0)
+    out = learned_leg(args, held_out=((256, "f64", full, args.learned_cap * 2, (1e-3,)),
+                                      (256, "f32", full, args.learned_cap * 2, (1e-3,)),
+                                      (1024, "f32", full, args.learned_cap_1024, (1e-3,))))
+    out["report"] = "learned"
     print(json.dumps(out), flush=True)
     return 0
 

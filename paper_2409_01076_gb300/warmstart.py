@@ -60,7 +60,13 @@ def generate_dataset(res, n: int = 256, tol: float = 1e-7, check_every: int = 10
             "converged": int((state == S.SMRT_BATCH_CONVERGED).sum()),
             "capped": int((state == S.SMRT_BATCH_CAPPED).sum()),
             "diverged": int((state == S.SMRT_BATCH_DIVERGED).sum()),
-            "steps_median": float(np.median(steps)), "steps_max": int(steps.max())}
+            "steps_median": float(np.median(steps)), "steps_max": int(steps.max()),
+            "residual_quantiles": {q: float(np.quantile(resid, v)) for q, v in
+                                   (("p50", 0.5), ("p90", 0.9), ("p99", 0.99), ("max", 1.0))}}
+    capped = resid[state == S.SMRT_BATCH_CAPPED]
+    if capped.size:
+        info["capped_residual_median"] = float(np.median(capped))
+        info["capped_re_min"] = float(min(re for re, st in zip(res, state) if st == S.SMRT_BATCH_CAPPED))
     return targets, info
 
 
@@ -159,3 +165,146 @@ def time_to_steady(res, n: int, net=None, tol: float = 1e-7, check_every: int = 
     S.smrt_batch_destroy(b)
     return {"steps": steps.tolist(), "state": state.tolist(), "residual": resid.tolist(), "wall_s": wall,
             "predict_s": t_pred}, fields
+
+
+def _u_of(h, n):
+    import torch
+    S = _S()
+    rho = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    u = torch.empty((2, n, n), dtype=torch.float64, device="cuda")
+    S.smrt_macros(h, rho, u)
+    return u
+
+
+class _Tracked:
+    """One cavity advanced in chunks of K updates on its own handle; after each chunk the stride
+    residual r = ||u(t) - u(t-K)|| / (K ||u(t)||) over all nodes.  Step time is taken with CUDA events
+    around the update launches only (the checks are outside it)."""
+
+    def __init__(self, n, re, K, prec):
+        import torch
+        S = _S()
+        self.n, self.K = n, K
+        self.h = S.smrt_create(n, n, W.cavity_tau(n, U_LID, re), U_LID, W.CAVITY)
+        S.smrt_set_option(self.h, S.SMRT_OPT_PRECISION, prec)
+        S.smrt_set_option(self.h, S.SMRT_OPT_CHECK_DIVERGENCE, 0)
+        self.t = 0
+        self.step_ms = 0.0
+        self.u_prev = _u_of(self.h, n)
+        self._ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+
+    def init(self, rho, u):
+        S = _S()
+        S.smrt_init_macros(self.h, rho, u)
+        self.u_prev = _u_of(self.h, self.n)
+
+    def advance(self):
+        import torch
+        S = _S()
+        a, b = self._ev
+        a.record()
+        S.smrt_step(self.h, self.K)
+        b.record()
+        self.t += self.K
+        u = _u_of(self.h, self.n)
+        torch.cuda.synchronize()
+        self.step_ms += a.elapsed_time(b)
+        norm = float(u.norm())
+        r = float((u - self.u_prev).norm()) / (self.K * norm) if norm > 0 else 0.0
+        self.u_prev = u
+        if not math.isfinite(r):
+            raise FloatingPointError("cavity diverged at t = %d" % self.t)
+        return u, r
+
+    def close(self):
+        _S().smrt_destroy(self.h)
+
+
+def _converge(tr, tol, ref_tol, ref_factor, max_steps):
+    """Advances a tracked cavity until its stride residual first falls below `tol` (steps_tol), then on
+    until it falls below `ref_tol` or steps_tol x ref_factor: its own converged field.  Returns the
+    velocity at every check (float32), steps_tol (None if capped), the final field, steps and residual."""
+    snaps, steps_tol, r = [], None, 1.0
+    while tr.t < max_steps:
+        u, r = tr.advance()
+        snaps.append(u.float())
+        if steps_tol is None and r < tol:
+            steps_tol = tr.t
+        if steps_tol is not None and (r < ref_tol or tr.t >= ref_factor * steps_tol):
+            break
+    return snaps, steps_tol, tr.u_prev, tr.t, r
+
+
+def time_to_same_error(net, res, n: int, prec: int = None, tol: float = 1e-7, ref_tol: float = 1e-11,
+                       levels=(), check_every: int = 1000, max_steps: int = 400000, train_n: int = 256,
+                       ref_factor: int = 6):
+    """Time to steady state at the same error, cold start vs learned warm start, per Re (n x n cavity).
+
+    Each run -- cold from rest, warm from f^eq of the network's prediction -- goes on past the plain
+    method's steady criterion (stride residual < `tol`) until its residual falls below `ref_tol` (four
+    decades lower) or its steps reach ref_factor times the criterion's: that is the run's own converged
+    field u_inf, decided by the plain solver alone.  The error of a run at step t is
+    e(t) = max over nodes |u(t) - u_inf| / U_lid.  The same error is the cold run's e at its criterion;
+    the warm run's time to steady is its first check with e at most that (and, for each of `levels`,
+    at most that level).  The two converged fields are compared as well (final_diff): the steady state
+    of this update with halfway bounce-back is not unique -- on the FP64 oracle a 32^2 cavity started
+    from a perturbed field settles 1e-3 U away from the cold start's, with its residual at rounding
+    level -- and in FP32 each run also freezes at its own fixed point once every correction rounds
+    away.  Wall times are steps x the measured per-update time of the lattice (CUDA events over the
+    update launches); the warm time adds the prediction (network, resampling, smrt_init_macros).
+    A run that does not reach `tol` within max_steps is reported as capped and left out."""
+    import torch
+    S = _S()
+    if prec is None:
+        prec = S.SMRT_PREC_F32
+    out = []
+    for re in res:
+        row = {"re": re, "n": n, "prec": {0: "f64", 1: "f32"}.get(prec, prec)}
+        cold = _Tracked(n, re, check_every, prec)
+        snaps_c, steps_cold, uinf_c, end_c, r_c = _converge(cold, tol, ref_tol, ref_factor, max_steps)
+        ms_per_step = cold.step_ms / max(cold.t, 1)
+        cold.close()
+        if steps_cold is None:
+            row.update(capped=True, cold_steps=end_c, cold_residual=r_c)
+            out.append(row)
+            continue
+        ref_c = uinf_c.float()
+        e_c = [float((x - ref_c).abs().amax()) / U_LID for x in snaps_c]
+        del snaps_c
+        e_cold = e_c[steps_cold // check_every - 1]
+
+        warm = _Tracked(n, re, check_every, prec)
+        torch.cuda.synchronize()
+        tp = time.perf_counter()
+        rho_p, u_p = predict_fields(net, [re], n, train_n)
+        warm.init(rho_p[0], u_p[0])
+        torch.cuda.synchronize()
+        predict_s = time.perf_counter() - tp
+        u_w0 = warm.u_prev.float()
+        snaps_w, steps_tol_w, uinf_w, end_w, r_w = _converge(warm, tol, ref_tol, ref_factor, max_steps)
+        warm.close()
+        ref_w = uinf_w.float()
+        e_w = [float((u_w0 - ref_w).abs().amax()) / U_LID] + \
+              [float((x - ref_w).abs().amax()) / U_LID for x in snaps_w]
+        del snaps_w
+        row.update(capped=False, cold_steps=steps_cold, cold_end_steps=end_c, cold_end_residual=r_c,
+                   cold_error=e_cold, warm_initial_error=e_w[0], warm_steps_tol=steps_tol_w,
+                   warm_end_steps=end_w, warm_end_residual=r_w,
+                   warm_error_at_tol=(e_w[steps_tol_w // check_every] if steps_tol_w else None),
+                   final_diff=float((uinf_w - uinf_c).abs().amax()) / U_LID,
+                   initial_diff=float((u_w0 - ref_c).abs().amax()) / U_LID,
+                   ms_per_step=ms_per_step, predict_s=predict_s, targets={})
+        for name, lv in [("same_error", e_cold)] + [("level_%g" % x, x) for x in levels]:
+            kc = next((i for i, e in enumerate(e_c) if e <= lv), None)
+            kw = next((i for i, e in enumerate(e_w) if e <= lv), None)
+            c = None if kc is None else (kc + 1) * check_every
+            w = None if kw is None else kw * check_every          # e_w[0] is the start, before any step
+            t = {"error": lv, "cold_steps": c, "warm_steps": w}
+            if c and w is not None:
+                t["cold_s"] = c * ms_per_step * 1e-3
+                t["warm_s"] = w * ms_per_step * 1e-3 + predict_s
+                t["steps_factor"] = c / max(w, check_every)
+                t["wall_factor"] = t["cold_s"] / t["warm_s"]
+            row["targets"][name] = t
+        out.append(row)
+    return out

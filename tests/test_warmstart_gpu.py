@@ -4,6 +4,8 @@ state as the cold start in fewer steps."""
 import numpy as np
 import pytest
 
+import paper_2409_01076_gb300 as S
+
 pytestmark = pytest.mark.gpu
 
 
@@ -30,3 +32,17 @@ def test_warm_start_reaches_the_same_steady_state_faster():
         assert warm["steps"][k] < cold["steps"][k], (cold["steps"], warm["steps"], err)
         # both runs end at the solver's own steady state, not the network's guess
         assert float((fc[k] - fw[k]).abs().max()) / WS.U_LID < 1e-3
+    # time to steady at the same error: each run's distance to its own converged field, the warm run
+    # against the error the plain method has at its own criterion
+    rows = WS.time_to_same_error(net, held, n, S.SMRT_PREC_F64, 1e-7, 1e-11, (1e-3,), 200, 400000, train_n=n)
+    for row in rows:
+        assert not row["capped"], row
+        assert row["cold_end_steps"] >= row["cold_steps"] and row["cold_end_residual"] < 1e-9, row
+        assert 0.0 < row["cold_error"] < 1e-3, row
+        assert row["warm_initial_error"] > row["cold_error"], row       # the guess alone is not enough
+        t = row["targets"]["same_error"]
+        assert t["cold_steps"] is not None and t["warm_steps"] is not None, row
+        assert t["warm_steps"] < t["cold_steps"], row
+        assert t["steps_factor"] > 1.0 and t["wall_factor"] > 1.0, row
+        assert row["targets"]["level_0.001"]["warm_steps"] is not None, row
+        assert row["final_diff"] < 1e-2, row
