@@ -99,6 +99,25 @@ SMRT_API long long smrt_nn_pack3_halves(int cout, int C);
  * wp: smrt_nn_pack3_halves(cout, C) halves, 16-byte aligned.  C % 16 == 0. */
 SMRT_API int smrt_nn_pack3(const void *w, int cout, int C, void *wp, void *stream);
 
+/* Every packed weight array of a network in one launch, straight from the float32 weights
+ * w (cout x 9 cin, column tap*cin + c).  Per descriptor:
+ *   kind SMRT_NN_PACK_FORWARD: dst = smrt_nn_pack3 of half(w) zero-padded to cpad >= cin input
+ *     channels (cpad % 16 == 0; cpad == cin: no padding), the operand of smrt_nn_conv3_tma
+ *     (smrt_nn_pack3_halves(cout, cpad) halves);
+ *   kind SMRT_NN_PACK_ADJOINT: dst = smrt_nn_pack3 of smrt_nn_flip3(w), the operand of the input
+ *     gradient (cin output channels over cout input channels; cout % 16 == 0;
+ *     smrt_nn_pack3_halves(cin, cout) halves).
+ * The results equal those of the separate conversion, padding, flip and pack calls bit for bit.
+ * count <= SMRT_NN_PACK_MAX; dst 16-byte aligned. */
+#define SMRT_NN_PACK_MAX 32
+enum { SMRT_NN_PACK_FORWARD = 0, SMRT_NN_PACK_ADJOINT = 1 };
+typedef struct {
+    const float *w;
+    void *dst;
+    int kind, cout, cin, cpad;
+} smrt_nn_pack3_desc;
+SMRT_API int smrt_nn_pack3_many(int count, const smrt_nn_pack3_desc *descs, void *stream);
+
 /* 3x3, stride 1, zero padding 1 convolution:
  *   y[p][o] = alpha * sum_{tap, c} x[n][yy+ky-1][xx+kx-1][c] * w[o][tap*C + c] + beta * y[p][o]
  * for p = (n*H + yy)*W + xx, with x given blocked as xb (C % 16 == 0) and w packed as wp.  y: N*H*W
@@ -134,6 +153,22 @@ SMRT_API int smrt_nn_conv3_tma_wait_test(const void *xb, int N, int H, int W, in
 SMRT_API int smrt_nn_conv3_tma_bias_act(const void *xb, int N, int H, int W, int C, const void *wp, int cout,
                                         const float *bias, int act, float *z, float *a, void *ab, int *err,
                                         void *stream);
+
+/* The input gradient of a convolution B fused with the SiLU backward of the convolution A whose
+ * activation B reads (the chain a = SiLU(z_A), z_B = conv3(a)): with d = conv3(dzb, flipped W_B), the
+ * smrt_nn_conv3_tma product of B's blocked half dz (C channels) and its flipped packed weights wp,
+ *   dz_A = d * SiLU'(z) (act != 0) or d (act == 0),   SiLU'(z) = s (1 + z (1 - s)), s = 1 / (1 + e^-z),
+ * written as blocked halves to dzb_out (cout channels, the layout smrt_nn_bias_act_bwd_blocked
+ * writes) and, when dz is not NULL, as float32 NHWC rows of cout; db (cout floats, may be NULL)
+ * accumulates the column sums of dz_A (A's bias gradient) -- per tile in shared memory, then one
+ * float32 atomic per channel and tile, so its last bits vary from run to run.  z: A's pre-activation,
+ * N*H*W rows of cout float32.  dzb_out, dz and db equal smrt_nn_conv3_tma followed by
+ * smrt_nn_bias_act_bwd_blocked (dzb_out and dz bit for bit, db up to summation order) without the
+ * float32 d ever going to memory.  err as in smrt_nn_conv3_tma.  cout % 8 == 0; z, dz, dzb_out
+ * 16-byte aligned. */
+SMRT_API int smrt_nn_conv3_tma_act_bwd(const void *dzb, int N, int H, int W, int C, const void *wp, int cout,
+                                       const float *z, int act, float *dz, float *db, void *dzb_out, int *err,
+                                       void *stream);
 
 /* Weight gradient of the same convolution, ACCUMULATED into gw (cout rows of ldg >= 9C float32):
  *   gw[o][tap*C + c] += alpha * sum_p x[n][yy+ky-1][xx+kx-1][c] * dz[p][o]

@@ -68,6 +68,9 @@ SIGNATURES = [
     ("smrt_nn_conv3_tma", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_int, ctypes.c_float,
                                   ctypes.c_float, c_void_p, c_int, c_void_p, c_void_p]),
     ("smrt_nn_check", c_int, [c_void_p, c_void_p]),
+    ("smrt_nn_pack3_many", c_int, [c_int, c_void_p, c_void_p]),
+    ("smrt_nn_conv3_tma_act_bwd", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_int, c_void_p, c_int,
+                                          c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("smrt_nn_conv3_tma_wait_test", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_int, c_void_p, c_int,
                                             c_void_p, c_double, c_void_p]),
     ("smrt_nn_conv3_tma_bias_act", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_int, c_void_p, c_int,

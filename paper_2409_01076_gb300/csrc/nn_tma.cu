@@ -62,14 +62,37 @@ static_assert(kTileRows * kTilePx == 128, "M = 128");
 
 int tile_n(int cout) { return cout <= 32 ? 32 : cout <= 64 ? 64 : 128; }
 
-// Fused epilogue of the forward convolution (on != 0): v = acc + bias[o]; z = v; a = SiLU(v) (or v);
-// ab = half(a) in the blocked layout.  Any of z, a, ab may be null; cout % 8 == 0.
+// Fused epilogues.  on == 1, forward: v = acc + bias[o]; z = v; a = SiLU(v) (or v); ab = half(a) in the
+// blocked layout (any of z, a, ab may be null).  on == 2, the input gradient of a convolution B whose
+// input is the activation of a convolution A (pre-activation zin, cout channels): d = acc * SiLU'(zin)
+// (or acc), z = d (fp32, may be null), ab = half(d) blocked, db[o] += sum over pixels of d (may be null).
+// cout % 8 == 0.
 struct Epi {
     const float *bias;
     float *z, *a;
     __half *ab;
     int act, on;
+    const float *zin;
+    float *db;
 };
+
+// Warp reduce-scatter of 32 values per lane: afterwards v[0] of lane l is the sum over the warp's lanes
+// of their v[l].  Each of the five steps keeps half of a lane's values and adds its partner's matching
+// half (31 shuffles).
+__device__ __forceinline__ float warp_reduce_scatter32(float v[32], int lane)
+{
+    #pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const bool upper = (lane & w) != 0;
+        #pragma unroll
+        for (int k = 0; k < w; ++k) {
+            const float send = upper ? v[k] : v[k + w];
+            const float keep = upper ? v[k + w] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+        }
+    }
+    return v[0];
+}
 
 __device__ __forceinline__ float sigm(float v) { return 1.0f / (1.0f + expf(-v)); }
 
@@ -236,9 +259,11 @@ conv3_tma_kernel(const __grid_constant__ CUtensorMap tmx, const __half *__restri
     __shared__ __align__(8) unsigned long long full[kFwdStages], empty[kFwdStages], done;
     __shared__ uint32_t tmem_holder;
     __shared__ int failed;
+    __shared__ float sdb[TN];                                   // on == 2: this tile's bias-gradient sums
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int x0 = blockIdx.x * kTilePx, y0 = blockIdx.y * kTileRows;
+    if (epi.on == 2 && threadIdx.x < TN) sdb[threadIdx.x] = 0.0f;
     const int img = blockIdx.z / ntn, nb = blockIdx.z % ntn, n0 = nb * TN;
     const int nchunks = C / kChunk;
     constexpr int kSB = fwd_stage_bytes<TN>();
@@ -293,8 +318,44 @@ conv3_tma_kernel(const __grid_constant__ CUtensorMap tmx, const __half *__restri
         for (int c = 0; c < TN; c += 32) {
             uint32_t r[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, r);
-            if (!valid) continue;
             const int col0 = n0 + c;
+            if (epi.on == 2) {
+                float v[32];
+                #pragma unroll
+                for (int j = 0; j < 32; j += 8) {
+                    const bool ok = valid && col0 + j < cout;
+                    #pragma unroll
+                    for (int e = 0; e < 8; ++e) v[j + e] = ok ? __uint_as_float(r[j + e]) : 0.0f;
+                    if (!ok) continue;
+                    if (epi.act) {
+                        const float4 *zq = reinterpret_cast<const float4 *>(epi.zin + pix * cout + col0 + j);
+                        const float4 z0 = zq[0], z1 = zq[1];
+                        const float zz[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
+                        #pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const float sg = sigm(zz[e]);
+                            v[j + e] *= sg * (1.0f + zz[e] * (1.0f - sg));
+                        }
+                    }
+                    if (epi.z) {
+                        float4 *q = reinterpret_cast<float4 *>(epi.z + pix * cout + col0 + j);
+                        q[0] = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                        q[1] = make_float4(v[j + 4], v[j + 5], v[j + 6], v[j + 7]);
+                    }
+                    __half2 h[4];
+                    #pragma unroll
+                    for (int e = 0; e < 4; ++e) h[e] = __floats2half2_rn(v[j + 2 * e], v[j + 2 * e + 1]);
+                    const size_t g = (size_t)(col0 + j) / 8, G = (size_t)cout / 8;
+                    *reinterpret_cast<uint4 *>(epi.ab + (((size_t)img * G + g) * H * W + (size_t)yy * W + xx) * 8) =
+                        *reinterpret_cast<uint4 *>(h);
+                }
+                if (epi.db) {
+                    const float sum = warp_reduce_scatter32(v, lane);
+                    atomicAdd(&sdb[c + lane], sum);
+                }
+                continue;
+            }
+            if (!valid) continue;
             if (epi.on) {
                 #pragma unroll
                 for (int j = 0; j < 32; j += 8) {
@@ -348,6 +409,10 @@ conv3_tma_kernel(const __grid_constant__ CUtensorMap tmx, const __half *__restri
                     *p = (beta != 0.0f) ? v + beta * *p : v;
                 }
             }
+        }
+        if (epi.on == 2 && epi.db) {
+            __syncthreads();                                    // every warp's sums are in sdb
+            if (threadIdx.x < TN && n0 + (int)threadIdx.x < cout) atomicAdd(epi.db + n0 + threadIdx.x, sdb[threadIdx.x]);
         }
     }
     teardown<TN>(tmem);
@@ -626,6 +691,51 @@ __global__ void pack3_kernel(const __half *__restrict__ w, int cout, int C, int 
     }
 }
 
+// One launch for many packed weight arrays (smrt_nn_pack3_many): the descriptors travel as a kernel
+// parameter; thread i of the concatenated index space finds its array and forms that element of
+// pack3(src) with src = half(w) padded (forward) or half(flip3(w)) (adjoint), as pack3_kernel does.
+struct PackSeg {
+    const float *w;
+    __half *dst;
+    long long start, total;
+    int kind, rows, C, TN, cin, cout;
+};
+struct PackPlan {
+    PackSeg seg[SMRT_NN_PACK_MAX];
+    int count;
+    long long total;
+};
+
+__global__ void pack3_many_kernel(const __grid_constant__ PackPlan plan)
+{
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < plan.total;
+         g += (long long)gridDim.x * blockDim.x) {
+        int k = 0;
+        while (k + 1 < plan.count && g >= plan.seg[k + 1].start) ++k;
+        const PackSeg &S = plan.seg[k];
+        const long long i = g - S.start;
+        const int nchunks = S.C / kChunk;
+        const int e = (int)(i & 7);
+        long long r = i >> 3;
+        const int row = (int)(r % S.TN);
+        r /= S.TN;
+        const int kg = (int)(r % 18);
+        r /= 18;
+        const int chunk = (int)(r % nchunks);
+        const int nb = (int)(r / nchunks);
+        const int o = nb * S.TN + row, tap = kg >> 1, c = chunk * kChunk + (kg & 1) * 8 + e;
+        float v = 0.0f;
+        if (o < S.rows) {
+            if (S.kind == SMRT_NN_PACK_FORWARD) {
+                if (c < S.cin) v = S.w[(size_t)o * 9 * S.cin + (size_t)tap * S.cin + c];
+            } else {                                           // flip3: src[o][tap*cout + c] = w[c][8 - tap][o]
+                v = S.w[((size_t)c * 9 + (8 - tap)) * S.cin + o];
+            }
+        }
+        S.dst[i] = __float2half(v);
+    }
+}
+
 int tma_fail(int code, const char *fmt, ...)
 {
     char buf[256];
@@ -728,6 +838,42 @@ extern "C" int smrt_nn_pack3(const void *w, int cout, int C, void *wp, void *str
     return SMRT_OK;
 }
 
+extern "C" int smrt_nn_pack3_many(int count, const smrt_nn_pack3_desc *descs, void *stream)
+{
+    if (count < 1 || count > SMRT_NN_PACK_MAX || !descs)
+        return tma_fail(SMRT_ERR_ARG, "smrt_nn_pack3_many: count %d outside 1..%d", count, SMRT_NN_PACK_MAX);
+    PackPlan plan;
+    plan.count = count;
+    long long start = 0;
+    for (int k = 0; k < count; ++k) {
+        const smrt_nn_pack3_desc &d = descs[k];
+        PackSeg &S = plan.seg[k];
+        const bool fwd = d.kind == SMRT_NN_PACK_FORWARD;
+        if (!d.w || !d.dst || (reinterpret_cast<uintptr_t>(d.dst) & 15) != 0 || d.cout < 1 || d.cin < 1 ||
+            (d.kind != SMRT_NN_PACK_FORWARD && d.kind != SMRT_NN_PACK_ADJOINT) ||
+            (fwd && (d.cpad < d.cin || d.cpad % kChunk != 0)) || (!fwd && d.cout % kChunk != 0))
+            return tma_fail(SMRT_ERR_ARG, "smrt_nn_pack3_many: bad descriptor %d (kind %d cout %d cin %d cpad %d)", k,
+                            d.kind, d.cout, d.cin, d.cpad);
+        S.w = d.w;
+        S.dst = (__half *)d.dst;
+        S.kind = d.kind;
+        S.rows = fwd ? d.cout : d.cin;                 // output channels of the packed operand
+        S.C = fwd ? d.cpad : d.cout;                   // its input channels
+        S.TN = tile_n(S.rows);
+        S.cin = d.cin;
+        S.cout = d.cout;
+        S.total = 9LL * S.C * ((S.rows + S.TN - 1) / S.TN) * S.TN;
+        S.start = start;
+        start += S.total;
+    }
+    plan.total = start;
+    const int blocks = (int)((start + 255) / 256 < 8192 ? (start + 255) / 256 : 8192);
+    pack3_many_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(plan);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return tma_fail(SMRT_ERR_CUDA, "smrt_nn_pack3_many: %s", cudaGetErrorString(e));
+    return SMRT_OK;
+}
+
 extern "C" int smrt_nn_to_half_blocked(const float *x, int N, int H, int W, int C, float scale, void *xb,
                                        void *stream)
 {
@@ -799,7 +945,7 @@ int conv3_tma_run(const char *name, const void *xb, int N, int H, int W, int C, 
     const __half *w = (const __half *)wp;
     cudaError_t e;
     const int TN = tile_n(cout);
-    const Epi plain{nullptr, nullptr, nullptr, nullptr, 0, 0};
+    const Epi plain{nullptr, nullptr, nullptr, nullptr, 0, 0, nullptr, nullptr};
     if (TN == 32)
         e = launch_conv3_tma<32>(tmx, w, N, H, W, C, cout, alpha, beta, y, ldy, err, s, plain, wait_ns, withhold);
     else if (TN == 64)
@@ -864,13 +1010,41 @@ extern "C" int smrt_nn_conv3_tma_bias_act(const void *xb, int N, int H, int W, i
         return tma_fail(SMRT_ERR_CUDA, "smrt_nn_conv3_tma_bias_act: tensor map rejected (%d)", (int)r);
     cudaStream_t s = (cudaStream_t)stream;
     const __half *w = (const __half *)wp;
-    const Epi epi{bias, z, a, (__half *)ab, act, 1};
+    const Epi epi{bias, z, a, (__half *)ab, act, 1, nullptr, nullptr};
     cudaError_t e;
     const int TN = tile_n(cout);
     if (TN == 32) e = launch_conv3_tma<32>(tmx, w, N, H, W, C, cout, 1.0f, 0.0f, nullptr, cout, err, s, epi);
     else if (TN == 64) e = launch_conv3_tma<64>(tmx, w, N, H, W, C, cout, 1.0f, 0.0f, nullptr, cout, err, s, epi);
     else e = launch_conv3_tma<128>(tmx, w, N, H, W, C, cout, 1.0f, 0.0f, nullptr, cout, err, s, epi);
     if (e != cudaSuccess) return tma_fail(SMRT_ERR_CUDA, "smrt_nn_conv3_tma_bias_act: %s", cudaGetErrorString(e));
+    return SMRT_OK;
+}
+
+extern "C" int smrt_nn_conv3_tma_act_bwd(const void *dzb, int N, int H, int W, int C, const void *wp, int cout,
+                                         const float *z, int act, float *dz, float *db, void *dzb_out, int *err,
+                                         void *stream)
+{
+    const uintptr_t al = reinterpret_cast<uintptr_t>(z) | reinterpret_cast<uintptr_t>(dz) |
+                         reinterpret_cast<uintptr_t>(dzb_out);
+    if (!blocked_args_ok(dzb, N, H, W, C) || C % kChunk != 0 || !wp || (act && !z) || !dzb_out || cout < 8 ||
+        cout % 8 != 0 || (al & 15) || (reinterpret_cast<uintptr_t>(wp) & 15) != 0 ||
+        (H + kTileRows - 1) / kTileRows > 65535 || (long long)N * ((cout + tile_n(cout) - 1) / tile_n(cout)) > 65535)
+        return tma_fail(SMRT_ERR_ARG,
+                        "smrt_nn_conv3_tma_act_bwd: bad arguments (N %d H %d W %d C %d cout %d; C %% 16 == 0, "
+                        "cout %% 8 == 0, 16-byte aligned z, dz, dzb_out)", N, H, W, C, cout);
+    CUtensorMap tmx;
+    CUresult r = blocked_map(&tmx, dzb, N, H, W, C, kHaloPx, kHaloRows, 2);
+    if (r != CUDA_SUCCESS)
+        return tma_fail(SMRT_ERR_CUDA, "smrt_nn_conv3_tma_act_bwd: tensor map rejected (%d)", (int)r);
+    cudaStream_t s = (cudaStream_t)stream;
+    const __half *w = (const __half *)wp;
+    const Epi epi{nullptr, dz, nullptr, (__half *)dzb_out, act, 2, z, db};
+    cudaError_t e;
+    const int TN = tile_n(cout);
+    if (TN == 32) e = launch_conv3_tma<32>(tmx, w, N, H, W, C, cout, 1.0f, 0.0f, nullptr, cout, err, s, epi);
+    else if (TN == 64) e = launch_conv3_tma<64>(tmx, w, N, H, W, C, cout, 1.0f, 0.0f, nullptr, cout, err, s, epi);
+    else e = launch_conv3_tma<128>(tmx, w, N, H, W, C, cout, 1.0f, 0.0f, nullptr, cout, err, s, epi);
+    if (e != cudaSuccess) return tma_fail(SMRT_ERR_CUDA, "smrt_nn_conv3_tma_act_bwd: %s", cudaGetErrorString(e));
     return SMRT_OK;
 }
 

@@ -82,6 +82,30 @@ def smrt_nn_conv3_tma(xb, nhwc, wp, y, cout, alpha=1.0, beta=0.0, err=None):
                                          float(beta), _p(y), int(y.shape[-1]), _p(err), _s()))
 
 
+SMRT_NN_PACK_FORWARD, SMRT_NN_PACK_ADJOINT = 0, 1
+
+
+class _PackDesc(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_void_p), ("dst", ctypes.c_void_p), ("kind", ctypes.c_int), ("cout", ctypes.c_int),
+                ("cin", ctypes.c_int), ("cpad", ctypes.c_int)]
+
+
+def smrt_nn_pack3_many(descs):
+    """descs: [(w float32 (cout, 9 cin), dst halves, kind, cout, cin, cpad)] -> every packed array in one launch."""
+    arr = (_PackDesc * len(descs))()
+    for k, (w, dst, kind, cout, cin, cpad) in enumerate(descs):
+        arr[k] = _PackDesc(w.data_ptr(), dst.data_ptr(), int(kind), int(cout), int(cin), int(cpad))
+    _check(_lib.load().smrt_nn_pack3_many(len(descs), arr, _s()))
+
+
+def smrt_nn_conv3_tma_act_bwd(dzb, nhwc, wp, cout, z, act, dz, db, dzb_out, err=None):
+    """Input gradient of B (blocked half dz of shape nhwc, flipped packed weights wp) fused with A's SiLU
+    backward: dzb_out (blocked halves, cout channels), dz (N*H*W x cout float32 or None), db += column sums."""
+    n, h, w, c = nhwc
+    _check(_lib.load().smrt_nn_conv3_tma_act_bwd(_p(dzb), int(n), int(h), int(w), int(c), _p(wp), int(cout), _p(z),
+                                                 int(act), _p(dz), _p(db), _p(dzb_out), _p(err), _s()))
+
+
 def smrt_nn_check(err):
     """Raises SmrtError(SMRT_ERR_TIMEOUT) (and resets err) if a tensor-core wait gave up; waits for the stream."""
     _check(_lib.load().smrt_nn_check(_p(err), _s()))

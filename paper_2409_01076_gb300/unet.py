@@ -50,6 +50,14 @@ def _pad8(n: int) -> int:
     return (n + 7) // 8 * 8
 
 
+class _DzPre:
+    """dL/dz of a convolution, already through its SiLU backward (and its bias gradient accumulated) by
+    the fused epilogue of the next convolution's input gradient: blocked halves, and float32 if needed."""
+
+    def __init__(self, dzf, dzb):
+        self.dzf, self.dzb = dzf, dzb
+
+
 class _Act:
     """An activation (N, H, W, C): its float32 NHWC tensor `f` and/or its blocked half copy `b`
     ([N][C/8][H][W][8], the operand layout of the TMA convolutions); either may be None."""
@@ -103,6 +111,9 @@ class UNet:
         if conv not in ("tma", "gather"):
             raise ValueError("conv must be 'tma' or 'gather'")
         self.conv_path = conv           # tcgen05 3x3 convolutions: TMA halo tiles, or thread-gathered A tiles
+        # the input gradient of a convolution that reads another's activation computes that one's SiLU
+        # backward and bias gradient in its epilogue (smrt_nn_conv3_tma_act_bwd)
+        self.fuse_act_bwd = True
         self._gemm_err = torch.zeros(1, dtype=torch.int32, device=device)   # tensor-core wait timeouts
 
     def _gemm(self, transA, transB, M, N, Kd, alpha, A, lda, B, ldb, beta, C, ldc, split=1):
@@ -132,7 +143,14 @@ class UNet:
         return sum(p.numel() for p in self.params.values())
 
     # ---- one convolution (3x3 via im2col, or 1x1) ----------------------------------------
+    def _all_tma(self):
+        """Every 3x3 convolution reads packed TMA operands, forward and (but for the input layer) adjoint."""
+        return all((self._tma(3, ci) or self._tma_padded(sp)) and (name == "enc1a" or self._tma(3, co))
+                   for sp in self.specs for name, ci, co, k, _ in [sp] if k == 3)
+
     def _half_weights(self):
+        if self._all_tma():
+            return self._packed_weights()
         t = self.torch
         self._wh, self._wf, self._wp, self._wfp = {}, {}, {}, {}
         for spec in self.specs:
@@ -156,6 +174,27 @@ class UNet:
                 if self._tma(k, co):
                     self._wfp[name] = t.empty(K.smrt_nn_pack3_halves(ci, co), dtype=t.float16, device=self.device)
                     K.smrt_nn_pack3(f, co, self._wfp[name])
+
+    def _packed_weights(self):
+        """The TMA path reads only packed halves: every layer's forward and adjoint operand in one launch
+        (smrt_nn_pack3_many) into buffers allocated once; the 1x1 head reads its float32 weights."""
+        t = self.torch
+        if getattr(self, "_pack_descs", None) is None:
+            self._wh, self._wf, self._wp, self._wfp = {}, {}, {}, {}
+            descs = []
+            for spec in self.specs:
+                name, ci, co, k, _ = spec
+                if k != 3:
+                    continue
+                w = self.params[name + ".w"]
+                cpad = 16 if self._tma_padded(spec) else ci
+                self._wp[name] = t.empty(K.smrt_nn_pack3_halves(co, cpad), dtype=t.float16, device=self.device)
+                descs.append((w, self._wp[name], K.SMRT_NN_PACK_FORWARD, co, ci, cpad))
+                if name != "enc1a" and self._tma(k, co):
+                    self._wfp[name] = t.empty(K.smrt_nn_pack3_halves(ci, co), dtype=t.float16, device=self.device)
+                    descs.append((w, self._wfp[name], K.SMRT_NN_PACK_ADJOINT, co, ci, ci))
+            self._pack_descs = descs
+        K.smrt_nn_pack3_many(self._pack_descs)
 
     def _conv(self, spec, inp, cache, out_f=True, out_b=False):
         """One convolution + bias + activation.  inp: _Act; returns an _Act with the float32 output
@@ -248,7 +287,19 @@ class UNet:
         _, ci, co, k, _ = spec
         return self._tma(k, ci) and co % 8 == 0
 
-    def _conv_bwd(self, spec, da, cache, need_dx=True):
+    def _fusable(self, spec_b, spec_a, cache):
+        """B's input gradient can carry A's SiLU backward in its epilogue (A's activation is B's input)."""
+        _, ci_b, co_b, k_b, _ = spec_b
+        name_a, _, co_a, k_a, act_a = spec_a
+        _, z_a, _, xb_a, _ = cache[name_a]
+        return (self.conv_path == "tma" and self.fuse_act_bwd and k_b == 3 and self._tma(3, co_b)
+                and co_a == ci_b and co_a % 8 == 0 and (z_a is not None or not act_a) and k_a == 3
+                and not self._small_1x1(spec_a))
+
+    def _conv_bwd(self, spec, da, cache, need_dx=True, then=None):
+        """Gradients of one convolution from dL/d(activation) `da` (a float32 tensor, or the _DzPre that the
+        consumer's fused input gradient produced).  Returns dL/d(input), or -- when `then` names the
+        convolution A whose activation is this one's input and the fusion applies -- A's _DzPre."""
         t = self.torch
         name, ci, co, k, act = spec
         col, z, xf, xb, xshape = cache[name]
@@ -264,13 +315,16 @@ class UNet:
         gw = self.grads[name + ".w"]
         tma_w = xb is not None and co % 8 == 0              # weight gradient from blocked halves
         tma_dx = need_dx and k == 3 and self._tma(k, co)    # input gradient by the TMA convolution
-        dzf = t.empty_like(da) if (not tma_w or (need_dx and not tma_dx)) else None
-        dzb = None
-        if tma_w or tma_dx:
-            dzb = t.empty(rows * co, dtype=t.float16, device=self.device)
-            K.smrt_nn_bias_act_bwd_blocked(da, z, act, dzf, self.grads[name + ".b"], dzb)
+        if isinstance(da, _DzPre):          # dz and the bias gradient came out of the consumer's epilogue
+            dzf, dzb = da.dzf, da.dzb
         else:
-            K.smrt_nn_bias_act_bwd(da, z, act, dzf, self.grads[name + ".b"])
+            dzf = t.empty_like(da) if (not tma_w or (need_dx and not tma_dx)) else None
+            dzb = None
+            if tma_w or tma_dx:
+                dzb = t.empty(rows * co, dtype=t.float16, device=self.device)
+                K.smrt_nn_bias_act_bwd_blocked(da, z, act, dzf, self.grads[name + ".b"], dzb)
+            else:
+                K.smrt_nn_bias_act_bwd(da, z, act, dzf, self.grads[name + ".b"])
         dzh = None
         if tma_w and xshape[3] != ci:
             # zero-padded input layer: the padded gradient, folded back onto the real channels
@@ -295,6 +349,16 @@ class UNet:
                 self._gemm(1, 0, co, kk, rows, 1.0, dzh, ldz, col, ldk, 1.0, gw, kk, split)
         if not need_dx:
             return None
+        if tma_dx and then is not None and self._fusable(spec, then, cache):
+            name_a, _, co_a, _, act_a = then
+            _, z_a, _, _, _ = cache[name_a]
+            # A needs float32 dz too unless both its gradients are TMA kernels reading the blocked halves
+            tma_a = cache[name_a][3] is not None and self._tma(3, co_a)
+            dzf_a = t.empty(xshape, dtype=t.float32, device=self.device) if not tma_a else None
+            dzb_a = t.empty(rows * co_a, dtype=t.float16, device=self.device)
+            K.smrt_nn_conv3_tma_act_bwd(dzb, (n, h, w, co), self._wfp[name], co_a, z_a, act_a, dzf_a,
+                                        self.grads[name_a + ".b"], dzb_a, self._gemm_err)
+            return _DzPre(dzf_a, dzb_a)
         dx = t.empty(xshape, dtype=t.float32, device=self.device)
         if k == 1:
             self._gemm(0, 0, rows, ci, co, 1.0, dzh, ldz, self._wh[name], ci, 0.0, dx, ci)
@@ -400,14 +464,18 @@ class UNet:
             K.smrt_nn_add(acc, other, acc)
             return acc
 
+        def pair(a, bname, da, need=True):
+            """A then B (B reads A's activation): B's input gradient carries A's SiLU backward."""
+            return self._conv_bwd(s[a], self._conv_bwd(s[bname], da, cache, True, then=s[a]), cache, need)
+
         dd1 = cb("head", dy)
-        du2, de1 = upcat_bwd(cb("dec1a", cb("dec1b", dd1)), 2 * b)
-        du3, de2 = upcat_bwd(cb("dec2a", cb("dec2b", du2)), 4 * b)
-        dum, de3 = upcat_bwd(cb("dec3a", cb("dec3b", du3)), 8 * b)
-        de3 = add_into(de3, pool_bwd(cb("mida", cb("midb", dum))))
-        de2 = add_into(de2, pool_bwd(cb("enc3a", cb("enc3b", de3))))
-        de1 = add_into(de1, pool_bwd(cb("enc2a", cb("enc2b", de2))))
-        cb("enc1a", cb("enc1b", de1), need=False)
+        du2, de1 = upcat_bwd(pair("dec1a", "dec1b", dd1), 2 * b)
+        du3, de2 = upcat_bwd(pair("dec2a", "dec2b", du2), 4 * b)
+        dum, de3 = upcat_bwd(pair("dec3a", "dec3b", du3), 8 * b)
+        de3 = add_into(de3, pool_bwd(pair("mida", "midb", dum)))
+        de2 = add_into(de2, pool_bwd(pair("enc3a", "enc3b", de3)))
+        de1 = add_into(de1, pool_bwd(pair("enc2a", "enc2b", de2)))
+        pair("enc1a", "enc1b", de1, need=False)
 
     def loss_and_grad(self, x, target):
         """MSE loss (float) with scaled gradients accumulated into self.grads (zeroed first)."""

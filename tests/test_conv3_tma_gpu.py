@@ -242,3 +242,72 @@ def test_wait_timeout_is_reported_and_the_next_call_runs():
     with pytest.raises(S.SmrtError) as ei:
         S.smrt_nn_conv3_tma_wait_test(xb, (n, h, w, C), wp, y, cout, err, wait_ms=0.0)
     assert ei.value.status == S.SMRT_ERR_ARG
+
+
+@pytest.mark.parametrize("act", [1, 0])
+@pytest.mark.parametrize("n,h,w,C,cout", [(2, 37, 21, 32, 16), (1, 32, 40, 64, 32), (2, 18, 10, 32, 136)])
+def test_conv3_tma_act_bwd_equals_the_unfused_pair(n, h, w, C, cout, act):
+    """The input gradient with the SiLU backward of the producing layer in its epilogue gives exactly the
+    blocked halves and float32 dz that smrt_nn_conv3_tma followed by smrt_nn_bias_act_bwd_blocked give,
+    and the same bias gradient up to summation order."""
+    import torch
+    r = _rng(700 + C + cout + act)
+    dz_b = r.normal(size=(n, h, w, C)).astype(np.float16)
+    wt = torch.tensor(r.normal(size=(cout, 9 * C)).astype(np.float16), device="cuda")
+    z = torch.tensor(r.normal(size=(n, h, w, cout)).astype(np.float32), device="cuda")
+    db0 = r.normal(size=cout).astype(np.float32)
+    xb = torch.tensor(_blocked(dz_b), device="cuda")
+    wp = torch.empty(S.smrt_nn_pack3_halves(cout, C), dtype=torch.float16, device="cuda")
+    S.smrt_nn_pack3(wt, C, wp)
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    # unfused
+    d = torch.empty((n, h, w, cout), device="cuda")
+    S.smrt_nn_conv3_tma(xb, (n, h, w, C), wp, d, cout, 1.0, 0.0, err)
+    dz1 = torch.empty_like(d)
+    dzb1 = torch.empty(d.numel(), dtype=torch.float16, device="cuda")
+    db1 = torch.tensor(db0, device="cuda")
+    S.smrt_nn_bias_act_bwd_blocked(d, z, act, dz1, db1, dzb1)
+    # fused
+    dz2 = torch.empty_like(d)
+    dzb2 = torch.empty_like(dzb1)
+    db2 = torch.tensor(db0, device="cuda")
+    S.smrt_nn_conv3_tma_act_bwd(xb, (n, h, w, C), wp, cout, z, act, dz2, db2, dzb2, err)
+    dzb3 = torch.empty_like(dzb1)
+    S.smrt_nn_conv3_tma_act_bwd(xb, (n, h, w, C), wp, cout, z, act, None, None, dzb3, err)
+    S.smrt_nn_check(err)
+    assert torch.equal(dz1, dz2) and torch.equal(dzb1, dzb2) and torch.equal(dzb1, dzb3)
+    ref = db1.cpu().numpy().astype(np.float64)
+    assert np.abs(db2.cpu().numpy() - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
+
+
+def test_pack3_many_equals_the_separate_calls():
+    """One launch for every packed array of a network gives the bits of the separate conversion, padding,
+    flip and pack calls: forward operands (one zero-padded input layer), adjoint operands, ragged tiles."""
+    import torch
+    r = _rng(55)
+    layers = [(32, 3, 16), (64, 32, 32), (48, 96, 96), (130, 32, 32), (256, 128, 128)]   # cout, cin, cpad
+    descs, expect = [], []
+    for cout, cin, cpad in layers:
+        w = torch.tensor(r.normal(size=(cout, 9 * cin)).astype(np.float32), device="cuda")
+        if cpad != cin:
+            wh = torch.empty((cout, 9 * cpad), dtype=torch.float16, device="cuda")
+            S.smrt_nn_pad3(w, cin, cpad, wh)
+        else:
+            wh = w.half()
+        ref = torch.empty(S.smrt_nn_pack3_halves(cout, cpad), dtype=torch.float16, device="cuda")
+        S.smrt_nn_pack3(wh, cpad, ref)
+        dst = torch.full_like(ref, float("nan"))
+        descs.append((w, dst, S.SMRT_NN_PACK_FORWARD, cout, cin, cpad))
+        expect.append((dst, ref))
+        if cout % 16 == 0:
+            f = torch.empty((cin, 9 * cout), dtype=torch.float16, device="cuda")
+            S.smrt_nn_flip3(w, f)
+            ref_a = torch.empty(S.smrt_nn_pack3_halves(cin, cout), dtype=torch.float16, device="cuda")
+            S.smrt_nn_pack3(f, cout, ref_a)
+            dst_a = torch.full_like(ref_a, float("nan"))
+            descs.append((w, dst_a, S.SMRT_NN_PACK_ADJOINT, cout, cin, cin))
+            expect.append((dst_a, ref_a))
+    S.smrt_nn_pack3_many(descs)
+    torch.cuda.synchronize()
+    for dst, ref in expect:
+        assert torch.equal(dst, ref)

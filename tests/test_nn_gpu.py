@@ -329,6 +329,31 @@ def test_unet_gradients_match_oracle_at_training_size(backend, conv):
         assert net.gemm_timeouts() == 0
 
 
+def test_fused_silu_backward_gives_the_unfused_gradients():
+    """The input gradients that carry the next layer's SiLU backward in their epilogue (the default) give
+    the gradients of the separate input-gradient and SiLU-backward kernels, up to the summation order of
+    the bias-gradient and weight-gradient atomics."""
+    from paper_2409_01076_gb300.unet import UNet
+    base, n, h = 32, 2, 64
+    params = U.init_params(base, seed=5)
+    r = _rng(14)
+    x = _t(r.uniform(0, 1, size=(n, h, h, 3)))
+    t = _t(0.3 * r.normal(size=(n, h, h, 3)))
+    grads = []
+    for fused in (True, False):
+        net = UNet(base=base)
+        net.fuse_act_bwd = fused
+        net.load_numpy(params)
+        net.grad_scale = 1024.0
+        net.loss_and_grad(x, t)
+        net.check_timeouts()
+        grads.append({k: _np(v).astype(np.float64) for k, v in net.grads.items()})
+    for key in grads[0]:
+        a, b = grads[0][key], grads[1][key]
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+        assert rel < 1e-5, (key, rel)
+
+
 def test_graph_replay_matches_eager_training():
     """Three Adam steps with the forward and backward pass replayed from one CUDA graph give the
     losses and parameters of three eager steps (up to the order of the weight-gradient atomics)."""
