@@ -267,8 +267,9 @@ SMRT_API int smrt_batch_set_stream(smrt_batch_t *b, void *stream);
  * threads per block, with or without a 64-register bound, each without (index k)
  * and with (index k + 5 for FP32 storage, k + 4 for FP64) the edge column groups
  * of the two-buffer layout in the vector path; then row-segmented shapes, whose
- * warps cover several rows of a narrow lattice at once (indices 10 to 12 for
- * FP32, 8 for FP64); FP32: 13 candidates, FP64: 9) on
+ * warps cover several rows of a narrow lattice at once (indices 10 to 14 for
+ * FP32, 13 and 14 with each block walking one contiguous run of the work list;
+ * 8 for FP64); FP32: 15 candidates, FP64: 9) on
  * `steps` steps of this batch, run on a copy of the state so no lattice advances,
  * and keeps the fastest; *choice (may be NULL) receives its index.  Allocates one
  * scratch copy of the populations for the duration. */

@@ -229,6 +229,13 @@ SMRT_API int smrt_nn_bias_act_blocked(const float *x, const float *bias, int N, 
                                       float *z, float *a, void *ab, void *stream);
 SMRT_API int smrt_nn_bias_act_bwd_blocked(const float *da, const float *z, int N, int H, int W, int C, int act,
                                           float *dz, float *db, void *dzb, void *stream);
+/* smrt_nn_bias_act_bwd_blocked of da + the 2x2 average-pooling adjoint of dp, in one pass: the encoder's
+ * activation gradient is the sum of its skip part da (N,H,W,C) and its pooled part dp (N,H/2,W/2,C), each
+ * of whose values goes to its four children times 1/4.  Equals smrt_nn_avgpool2_bwd, smrt_nn_add and
+ * smrt_nn_bias_act_bwd_blocked in turn bit for bit (db up to summation order); H and W even. */
+SMRT_API int smrt_nn_bias_act_bwd_addpool_blocked(const float *da, const float *dp, const float *z, int N, int H,
+                                                  int W, int C, int act, float *dz, float *db, void *dzb,
+                                                  void *stream);
 SMRT_API int smrt_nn_avgpool2_blocked(const float *x, int N, int H, int W, int C, float *y, void *yb, void *stream);
 SMRT_API int smrt_nn_upcat(const float *a, int N, int H, int W, int Ca, const float *b, int Cb, float *y, void *yb,
                            void *stream);

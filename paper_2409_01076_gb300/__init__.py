@@ -321,7 +321,7 @@ from .nn import (smrt_nn_adam, smrt_nn_add, smrt_nn_avgpool2, smrt_nn_avgpool2_b
                  smrt_nn_bias_act_bwd, smrt_nn_col2im3, smrt_nn_concat, smrt_nn_concat_bwd, smrt_nn_flip3, smrt_nn_gemm,
                  smrt_nn_gemm_tc, smrt_nn_conv3_tc, smrt_nn_conv3_tma, smrt_nn_conv3_wgrad_tma, smrt_nn_conv3_tma_bias_act,
                  smrt_nn_check, smrt_nn_conv3_tma_wait_test, smrt_nn_conv3_tma_act_bwd, smrt_nn_pack3_many,
-                 SMRT_NN_PACK_FORWARD, SMRT_NN_PACK_ADJOINT,
+                 SMRT_NN_PACK_FORWARD, SMRT_NN_PACK_ADJOINT, smrt_nn_bias_act_bwd_addpool_blocked,
                  smrt_nn_pack3, smrt_nn_pack3_halves, smrt_nn_to_half_blocked, smrt_nn_bias_act_blocked,
                  smrt_nn_to_half_blocked_pad, smrt_nn_pad3, smrt_nn_unpad3_add,
                  smrt_nn_bias_act_bwd_blocked, smrt_nn_avgpool2_blocked, smrt_nn_upcat, smrt_nn_upcat_bwd,

@@ -88,6 +88,8 @@ SIGNATURES = [
                                          c_void_p, c_void_p]),
     ("smrt_nn_bias_act_bwd_blocked", c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_int, c_void_p,
                                              c_void_p, c_void_p, c_void_p]),
+    ("smrt_nn_bias_act_bwd_addpool_blocked", c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_int,
+                                                     c_void_p, c_void_p, c_void_p, c_void_p]),
     ("smrt_nn_avgpool2_blocked", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     ("smrt_nn_upcat", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     ("smrt_nn_upcat_bwd", c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),

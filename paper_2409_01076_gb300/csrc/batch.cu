@@ -53,7 +53,7 @@ __device__ __forceinline__ void cp_async_wait_all()
 // compiler takes what the step needs and fewer blocks are resident.
 // EDGE: the two-buffer step also runs the edge column groups in the vector path (their geometry
 // must say so); without it those columns stay in the band and the vector path carries no edge code.
-template <int PREC, int KIND, int MODE, int VEC, int BX, bool CAP, bool EDGE, bool ROWSEG = false>
+template <int PREC, int KIND, int MODE, int VEC, int BX, bool CAP, bool EDGE, bool ROWSEG = false, bool CHUNK = false>
 __global__ void __launch_bounds__(BX, CAP ? 1024 / BX : 1)
 batch_step_kernel(const typename Prec<PREC>::R *src, typename Prec<PREC>::R *dst,
                   const BatchCav<typename Prec<PREC>::C> *__restrict__ cav, const int2 *__restrict__ work,
@@ -62,27 +62,33 @@ batch_step_kernel(const typename Prec<PREC>::R *src, typename Prec<PREC>::R *dst
     using Cav = BatchCav<typename Prec<PREC>::C>;
     static_assert(sizeof(Cav) % 8 == 0 && alignof(Cav) >= 8, "lattice record copied in 8-byte words");
     constexpr int kWords = (int)(sizeof(Cav) / 8);
-    // The lattice record of the running tile sits in shared memory (buffer `buf`).  The work list
-    // is read two tiles ahead; when the next tile belongs to another lattice its record is copied
-    // into the other buffer with cp.async while this tile runs.  So neither the work list nor the
-    // record is a dependent load in front of a tile's population loads, and the block
-    // synchronises only where its walk crosses from one lattice to another.
+    // A block walks the work list with the grid's stride (concurrent blocks hold neighbouring tiles,
+    // whose rows they share in L2), or with CHUNK one contiguous run of ceil(total / grid) tiles (the
+    // lattice rarely changes between consecutive tiles: better for many small lattices).  The
+    // lattice record of the running tile sits in shared memory (buffer `buf`).  The work list is
+    // read two tiles ahead; when the next tile belongs to another lattice its record is copied into
+    // the other buffer with cp.async while this tile runs.  So neither the work list nor the record
+    // is a dependent load in front of a tile's population loads, and the block synchronises only
+    // where its walk crosses from one lattice to another.
     __shared__ __align__(16) unsigned long long rec[2][kWords];
     const int total = counts[1];
     const int G = gridDim.x;
-    int t = blockIdx.x;
-    if (t >= total) return;
+    const int run = CHUNK ? (total + G - 1) / G : 0;
+    const int stride = CHUNK ? 1 : G;
+    int t = CHUNK ? blockIdx.x * run : blockIdx.x;
+    const int tend = CHUNK ? min(t + run, total) : total;
+    if (t >= tend) return;
     int2 w = work[t];
     for (int k = threadIdx.x; k < kWords; k += BX)
         rec[0][k] = reinterpret_cast<const unsigned long long *>(cav + w.x)[k];
     __syncthreads();
     int buf = 0;
-    int tn = t + G;
-    int2 wn = (tn < total) ? work[tn] : w;
+    int tn = t + stride;
+    int2 wn = (tn < tend) ? work[tn] : w;
     for (;;) {
-        const int tnn = tn + G;
-        const int2 wnn = (tnn < total) ? work[tnn] : wn;
-        const bool next = tn < total;
+        const int tnn = tn + stride;
+        const int2 wnn = (tnn < tend) ? work[tnn] : wn;
+        const bool next = tn < tend;
         const bool swap = next && wn.x != w.x;          // block-uniform
         if (swap) {
             const unsigned long long *g = reinterpret_cast<const unsigned long long *>(cav + wn.x);
@@ -196,16 +202,18 @@ struct Shape {
     bool cap;     // 64-register bound
     bool edge;    // edge column groups in the vector path (two-buffer layout)
     bool rowseg;  // row-segmented interior blocks
+    bool chunk;   // each block walks one contiguous run of the work list
 };
 template <int PREC> struct Shapes;
 template <> struct Shapes<SMRT_PREC_F32> {
-    static constexpr int nbase = 5, nseg = 3, n = 2 * nbase + nseg;
+    static constexpr int nbase = 5, nseg = 5, n = 2 * nbase + nseg;
     static Shape at(int k)
     {
         const Shape s[nbase] = {{4, 128, true, false, false}, {4, 64, true, false, false},
                                 {4, 256, true, false, false}, {2, 128, true, false, false},
                                 {4, 128, false, false, false}};
-        const Shape g[nseg] = {{4, 128, true, true, true}, {4, 128, false, true, true}, {4, 256, true, true, true}};
+        const Shape g[nseg] = {{4, 128, true, true, true}, {4, 128, false, true, true}, {4, 256, true, true, true},
+                               {4, 128, true, true, true, true}, {4, 256, true, true, true, true}};
         if (k >= 2 * nbase) return g[k - 2 * nbase];
         Shape r = s[k % nbase];
         r.edge = k >= nbase;
@@ -226,12 +234,13 @@ template <> struct Shapes<SMRT_PREC_F64> {
     }
 };
 
-template <int PREC, int KIND, int MODE, int VEC, int BX, bool CAP = true, bool EDGE = false, bool ROWSEG = false>
+template <int PREC, int KIND, int MODE, int VEC, int BX, bool CAP = true, bool EDGE = false, bool ROWSEG = false,
+          bool CHUNK = false>
 cudaError_t launch_batch_step_shape(const void *src, void *dst, const void *cav, const int2 *work,
                                     const int *counts, int sms, cudaStream_t s)
 {
     using P = Prec<PREC>;
-    auto kern = batch_step_kernel<PREC, KIND, MODE, VEC, BX, CAP, EDGE, ROWSEG>;
+    auto kern = batch_step_kernel<PREC, KIND, MODE, VEC, BX, CAP, EDGE, ROWSEG, CHUNK>;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BX, 0);
     if (e != cudaSuccess) return e;
@@ -265,6 +274,12 @@ cudaError_t launch_batch_step_m(int shape, const void *src, void *dst, const voi
             return launch_batch_step_shape<PREC, KIND, MODE, 4, 128, false, E, true>(src, dst, cav, work, counts, sms, s);
         case 12:
             return launch_batch_step_shape<PREC, KIND, MODE, 4, 256, true, E, true>(src, dst, cav, work, counts, sms, s);
+        case 13:
+            return launch_batch_step_shape<PREC, KIND, MODE, 4, 128, true, E, true, true>(src, dst, cav, work, counts,
+                                                                                          sms, s);
+        case 14:
+            return launch_batch_step_shape<PREC, KIND, MODE, 4, 256, true, E, true, true>(src, dst, cav, work, counts,
+                                                                                          sms, s);
         }
     } else {
         switch (shape) {

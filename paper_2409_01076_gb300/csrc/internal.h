@@ -74,7 +74,7 @@ const KernelTable &kernels_bf16();
 cudaError_t vec_bias_act(const float *x, const float *bias, long long rows, int C, int act, float *z, float *a,
                          __half *ab, int HW, cudaStream_t s);
 cudaError_t vec_bias_act_bwd(const float *da, const float *z, long long rows, int C, int act, float *dz, float *db,
-                             __half *dzb, int HW, cudaStream_t s);
+                             __half *dzb, int HW, cudaStream_t s, const float *dp = nullptr, int W = 0);
 cudaError_t vec_avgpool2(const float *x, int N, int H, int W, int C, float *y, __half *yb, cudaStream_t s);
 cudaError_t vec_avgpool2_bwd(const float *dy, int N, int H, int W, int C, float *dx, cudaStream_t s);
 cudaError_t vec_add(const float *a, const float *b, long long n, float *y, cudaStream_t s);

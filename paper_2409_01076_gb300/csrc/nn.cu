@@ -587,6 +587,20 @@ int smrt_nn_bias_act_bwd_blocked(const float *da, const float *z, int N, int H, 
     return vec_done(e, "smrt_nn_bias_act_bwd_blocked");
 }
 
+int smrt_nn_bias_act_bwd_addpool_blocked(const float *da, const float *dp, const float *z, int N, int H, int W, int C,
+                                         int act, float *dz, float *db, void *dzb, void *stream)
+{
+    if (!da || !dp || (act && !z) || N < 1 || H < 2 || W < 2 || (H & 1) || (W & 1) || C < 8 || C % 8 != 0 ||
+        C > 4096 || (long long)N * H * W * C >= (1LL << 31))
+        return nn_fail(SMRT_ERR_ARG, "smrt_nn_bias_act_bwd_addpool_blocked: bad arguments (N %d H %d W %d C %d; even H "
+                       "and W, C %% 8 == 0)", N, H, W, C);
+    const cudaError_t e = smrt::vec_bias_act_bwd(da, z, (long long)N * H * W, C, act, dz, db, (__half *)dzb, H * W,
+                                                 (cudaStream_t)stream, dp, W);
+    if (e == cudaErrorNotSupported)
+        return nn_fail(SMRT_ERR_ARG, "smrt_nn_bias_act_bwd_addpool_blocked: misaligned pointer");
+    return vec_done(e, "smrt_nn_bias_act_bwd_addpool_blocked");
+}
+
 int smrt_nn_avgpool2_blocked(const float *x, int N, int H, int W, int C, float *y, void *yb, void *stream)
 {
     if (!x || N < 1 || H < 2 || W < 2 || (H & 1) || (W & 1) || C < 8 || C % 8 != 0)

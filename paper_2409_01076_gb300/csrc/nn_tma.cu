@@ -708,14 +708,15 @@ struct PackPlan {
 
 __global__ void pack3_many_kernel(const __grid_constant__ PackPlan plan)
 {
-    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < plan.total;
-         g += (long long)gridDim.x * blockDim.x) {
+    // one thread per 8 consecutive halves (one 16-byte store): the eight share every index
+    for (long long g8 = blockIdx.x * (long long)blockDim.x + threadIdx.x; g8 < (plan.total >> 3);
+         g8 += (long long)gridDim.x * blockDim.x) {
+        const long long g = g8 << 3;
         int k = 0;
         while (k + 1 < plan.count && g >= plan.seg[k + 1].start) ++k;
         const PackSeg &S = plan.seg[k];
         const long long i = g - S.start;
         const int nchunks = S.C / kChunk;
-        const int e = (int)(i & 7);
         long long r = i >> 3;
         const int row = (int)(r % S.TN);
         r /= S.TN;
@@ -723,16 +724,22 @@ __global__ void pack3_many_kernel(const __grid_constant__ PackPlan plan)
         r /= 18;
         const int chunk = (int)(r % nchunks);
         const int nb = (int)(r / nchunks);
-        const int o = nb * S.TN + row, tap = kg >> 1, c = chunk * kChunk + (kg & 1) * 8 + e;
-        float v = 0.0f;
-        if (o < S.rows) {
-            if (S.kind == SMRT_NN_PACK_FORWARD) {
-                if (c < S.cin) v = S.w[(size_t)o * 9 * S.cin + (size_t)tap * S.cin + c];
-            } else {                                           // flip3: src[o][tap*cout + c] = w[c][8 - tap][o]
-                v = S.w[((size_t)c * 9 + (8 - tap)) * S.cin + o];
+        const int o = nb * S.TN + row, tap = kg >> 1, c0 = chunk * kChunk + (kg & 1) * 8;
+        __align__(16) __half v[8];
+        #pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            float x = 0.0f;
+            const int c = c0 + e;
+            if (o < S.rows) {
+                if (S.kind == SMRT_NN_PACK_FORWARD) {
+                    if (c < S.cin) x = S.w[(size_t)o * 9 * S.cin + (size_t)tap * S.cin + c];
+                } else {                                       // flip3: src[o][tap*cout + c] = w[c][8 - tap][o]
+                    x = S.w[((size_t)c * 9 + (8 - tap)) * S.cin + o];
+                }
             }
+            v[e] = __float2half(x);
         }
-        S.dst[i] = __float2half(v);
+        *reinterpret_cast<uint4 *>(S.dst + i) = *reinterpret_cast<const uint4 *>(v);
     }
 }
 
@@ -866,8 +873,9 @@ extern "C" int smrt_nn_pack3_many(int count, const smrt_nn_pack3_desc *descs, vo
         S.start = start;
         start += S.total;
     }
-    plan.total = start;
-    const int blocks = (int)((start + 255) / 256 < 8192 ? (start + 255) / 256 : 8192);
+    plan.total = start;                                // every segment is a multiple of 8 halves
+    const long long groups = start >> 3;
+    const int blocks = (int)((groups + 255) / 256 < 8192 ? (groups + 255) / 256 : 8192);
     pack3_many_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(plan);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return tma_fail(SMRT_ERR_CUDA, "smrt_nn_pack3_many: %s", cudaGetErrorString(e));

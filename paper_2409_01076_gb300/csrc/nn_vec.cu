@@ -90,8 +90,11 @@ __global__ void bias_act_vec(const float *__restrict__ x, const float *__restric
 // The grid stride is a multiple of G = C / V, so every thread keeps one channel group and sums its
 // share of db in registers; a block adds its per-channel sums with one atomic each.
 template <int V>
+// dp (may be NULL): a gradient at half resolution whose 2x2 average-pooling adjoint (0.25 dp of the
+// parent pixel) is added to da first; W is the full-resolution width.
 __global__ void bias_act_bwd_vec(const float *__restrict__ da, const float *__restrict__ z, int P, int C, int act,
-                                 float *dz, float *db, __half *__restrict__ dzb, int HW)
+                                 float *dz, float *db, __half *__restrict__ dzb, int HW,
+                                 const float *__restrict__ dp = nullptr, int W = 0)
 {
     extern __shared__ float sdb[];          // C floats
     for (int c = threadIdx.x; c < C; c += blockDim.x) sdb[c] = 0.0f;
@@ -106,6 +109,12 @@ __global__ void bias_act_bwd_vec(const float *__restrict__ da, const float *__re
         const int p = t / G;
         const size_t off = (size_t)p * C + (size_t)g * V;
         Vec<V> d = ldv<V>(da + off);
+        if (dp) {
+            const int n = p / HW, r = p - n * HW, yy = r / W, xx = r - yy * W;
+            const Vec<V> q = ldv<V>(dp + (((size_t)n * (HW / W / 2) + yy / 2) * (W / 2) + xx / 2) * C + (size_t)g * V);
+            #pragma unroll
+            for (int i = 0; i < V; ++i) d.v[i] += 0.25f * q.v[i];
+        }
         if (act) {
             const Vec<V> zz = ldv<V>(z + off);
             #pragma unroll
@@ -361,18 +370,19 @@ cudaError_t vec_bias_act(const float *x, const float *bias, long long rows, int 
 }
 
 cudaError_t vec_bias_act_bwd(const float *da, const float *z, long long rows, int C, int act, float *dz, float *db,
-                             __half *dzb, int HW, cudaStream_t s)
+                             __half *dzb, int HW, cudaStream_t s, const float *dp, int W)
 {
     const int V = (C % 8 == 0) ? 8 : (C % 4 == 0 ? 4 : 0);
     if (!V || (dzb && V != 8) || C > 4096 || rows * C >= (1LL << 31) || !al16(da) || (z && !al16(z)) ||
-        (dz && !al16(dz)) || (dzb && !al16(dzb)))
+        (dz && !al16(dz)) || (dzb && !al16(dzb)) || (dp && (!al16(dp) || W < 2 || W % 2 || HW % W || (HW / W) % 2)))
         return cudaErrorNotSupported;
     const int G = C / V;
     const unsigned blocks = blocks_for_groups(rows * G, G);
     if (V == 8)
-        bias_act_bwd_vec<8><<<blocks, 256, C * sizeof(float), s>>>(da, z, (int)rows, C, act, dz, db, dzb, HW);
+        bias_act_bwd_vec<8><<<blocks, 256, C * sizeof(float), s>>>(da, z, (int)rows, C, act, dz, db, dzb, HW, dp, W);
     else
-        bias_act_bwd_vec<4><<<blocks, 256, C * sizeof(float), s>>>(da, z, (int)rows, C, act, dz, db, nullptr, HW);
+        bias_act_bwd_vec<4><<<blocks, 256, C * sizeof(float), s>>>(da, z, (int)rows, C, act, dz, db, nullptr, HW, dp,
+                                                                    W);
     return cudaGetLastError();
 }
 

@@ -231,6 +231,13 @@ def smrt_nn_bias_act_bwd_blocked(da, z, act, dz, db, dzb):
                                                     _s()))
 
 
+def smrt_nn_bias_act_bwd_addpool_blocked(da, dp, z, act, dz, db, dzb):
+    """smrt_nn_bias_act_bwd_blocked of da (N, H, W, C) + the pooling adjoint of dp (N, H/2, W/2, C)."""
+    n, h, w, c = da.shape
+    _check(_lib.load().smrt_nn_bias_act_bwd_addpool_blocked(_p(da), _p(dp), _p(z), n, h, w, c, int(act), _p(dz),
+                                                            _p(db), _p(dzb), _s()))
+
+
 def smrt_nn_avgpool2_blocked(x, y, yb):
     """x: (N, H, W, C) float32; y: (N, H/2, W/2, C) float32 or None; yb: blocked halves or None."""
     n, h, w, c = x.shape

@@ -58,6 +58,14 @@ class _DzPre:
         self.dzf, self.dzb = dzf, dzb
 
 
+class _DaSum:
+    """An activation gradient given as its skip part (full resolution) plus its pooled part (half
+    resolution, to go through the 2x2 average-pooling adjoint): summed inside the SiLU backward."""
+
+    def __init__(self, skip, pooled):
+        self.skip, self.pooled = skip, pooled
+
+
 class _Act:
     """An activation (N, H, W, C): its float32 NHWC tensor `f` and/or its blocked half copy `b`
     ([N][C/8][H][W][8], the operand layout of the TMA convolutions); either may be None."""
@@ -317,7 +325,16 @@ class UNet:
         tma_dx = need_dx and k == 3 and self._tma(k, co)    # input gradient by the TMA convolution
         if isinstance(da, _DzPre):          # dz and the bias gradient came out of the consumer's epilogue
             dzf, dzb = da.dzf, da.dzb
+        elif isinstance(da, _DaSum) and (tma_w or tma_dx) and co % 8 == 0:
+            dzf = t.empty_like(da.skip) if (not tma_w or (need_dx and not tma_dx)) else None
+            dzb = t.empty(rows * co, dtype=t.float16, device=self.device)
+            K.smrt_nn_bias_act_bwd_addpool_blocked(da.skip, da.pooled, z, act, dzf, self.grads[name + ".b"], dzb)
         else:
+            if isinstance(da, _DaSum):
+                pooled = t.empty_like(da.skip)
+                K.smrt_nn_avgpool2_bwd(da.pooled, tuple(da.skip.shape), pooled)
+                K.smrt_nn_add(da.skip, pooled, da.skip)
+                da = da.skip
             dzf = t.empty_like(da) if (not tma_w or (need_dx and not tma_dx)) else None
             dzb = None
             if tma_w or tma_dx:
@@ -472,9 +489,16 @@ class UNet:
         du2, de1 = upcat_bwd(pair("dec1a", "dec1b", dd1), 2 * b)
         du3, de2 = upcat_bwd(pair("dec2a", "dec2b", du2), 4 * b)
         dum, de3 = upcat_bwd(pair("dec3a", "dec3b", du3), 8 * b)
-        de3 = add_into(de3, pool_bwd(pair("mida", "midb", dum)))
-        de2 = add_into(de2, pool_bwd(pair("enc3a", "enc3b", de3)))
-        de1 = add_into(de1, pool_bwd(pair("enc2a", "enc2b", de2)))
+        if self.fuse_act_bwd:
+            # each encoder level's activation gradient = its skip part + the pooled level's input
+            # gradient through the pooling adjoint, summed inside the SiLU backward
+            de3 = _DaSum(de3, pair("mida", "midb", dum))
+            de2 = _DaSum(de2, pair("enc3a", "enc3b", de3))
+            de1 = _DaSum(de1, pair("enc2a", "enc2b", de2))
+        else:
+            de3 = add_into(de3, pool_bwd(pair("mida", "midb", dum)))
+            de2 = add_into(de2, pool_bwd(pair("enc3a", "enc3b", de3)))
+            de1 = add_into(de1, pool_bwd(pair("enc2a", "enc2b", de2)))
         pair("enc1a", "enc1b", de1, need=False)
 
     def loss_and_grad(self, x, target):

@@ -311,3 +311,28 @@ def test_pack3_many_equals_the_separate_calls():
     torch.cuda.synchronize()
     for dst, ref in expect:
         assert torch.equal(dst, ref)
+
+
+@pytest.mark.parametrize("act", [1, 0])
+def test_bias_act_bwd_addpool_equals_pool_add_then_bias_act_bwd(act):
+    """The encoder's SiLU backward of (skip part + pooling adjoint of the pooled part) in one pass equals
+    avgpool2_bwd, add and bias_act_bwd_blocked in turn (dz and its halves bit for bit, db up to order)."""
+    import torch
+    n, h, w, c = 2, 20, 14, 48
+    r = _rng(31 + act)
+    da = torch.tensor(r.normal(size=(n, h, w, c)).astype(np.float32), device="cuda")
+    dp = torch.tensor(r.normal(size=(n, h // 2, w // 2, c)).astype(np.float32), device="cuda")
+    z = torch.tensor(r.normal(size=(n, h, w, c)).astype(np.float32), device="cuda")
+    db0 = r.normal(size=c).astype(np.float32)
+    up = torch.empty_like(da)
+    S.smrt_nn_avgpool2_bwd(dp, (n, h, w, c), up)
+    s = torch.empty_like(da)
+    S.smrt_nn_add(da, up, s)
+    dz1, dzb1, db1 = torch.empty_like(da), torch.empty(da.numel(), dtype=torch.float16, device="cuda"), \
+        torch.tensor(db0, device="cuda")
+    S.smrt_nn_bias_act_bwd_blocked(s, z, act, dz1, db1, dzb1)
+    dz2, dzb2, db2 = torch.empty_like(da), torch.empty_like(dzb1), torch.tensor(db0, device="cuda")
+    S.smrt_nn_bias_act_bwd_addpool_blocked(da, dp, z, act, dz2, db2, dzb2)
+    torch.cuda.synchronize()
+    assert torch.equal(dz1, dz2) and torch.equal(dzb1, dzb2)
+    assert np.abs(db1.cpu().numpy() - db2.cpu().numpy()).max() <= 1e-5 * max(1.0, np.abs(db0).max())
