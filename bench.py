@@ -865,6 +865,9 @@ def precision_report(args):
 
     def gpu_u(n, re, steps, prec, layout=0):
         h = S.smrt_create(n, n, W.cavity_tau(n, 0.1, re), 0.1, W.CAVITY)
+        if prec.endswith("-sr"):
+            prec = prec[:-3]
+            S.smrt_set_option(h, S.SMRT_OPT_ROUNDING, S.SMRT_ROUND_STOCHASTIC)
         S.smrt_set_option(h, S.SMRT_OPT_PRECISION, precs[prec])
         S.smrt_set_option(h, S.SMRT_OPT_LAYOUT, layout)
         S.smrt_step(h, steps)
@@ -882,21 +885,21 @@ def precision_report(args):
         wl = dict(name="cavity8192", nx=8192, ny=8192, tau=W.cavity_tau(8192, 0.1, re), u_lid=0.1, bc=W.CAVITY,
                   u0=None, desc="")
         thr = {}
-        for prec in ("f32", "f16", "bf16"):
+        for prec in ("f32", "f16", "bf16", "f16-sr", "bf16-sr"):
             for layout in ("ab", "aa"):
                 thr["%s-%s" % (prec, layout)] = run_variant(S, wl, None, None, prec, layout, "smrt",
                                                             args.variant_steps or 1000, 10, 1)
         entry["throughput_8192"] = thr
         u64_long = gpu_u(n_err, re, s_long, "f64")
         long_err = {}
-        for prec in ("f32", "f16", "bf16"):
+        for prec in ("f32", "f16", "bf16", "f16-sr", "bf16-sr"):
             d = gpu_u(n_err, re, s_long, prec) - u64_long
             long_err[prec] = {"max": float(np.abs(d).max() / 0.1), "rms": float(np.sqrt((d * d).mean()) / 0.1)}
         entry["error_vs_gpu_f64_long"] = long_err
         entry["gpu_f64_speed_max"] = float(np.abs(u64_long).max())
         u_ref = pending[re].get()
         short_err = {}
-        for prec in ("f64", "f32", "f16", "bf16"):
+        for prec in ("f64", "f32", "f16", "bf16", "f16-sr", "bf16-sr"):
             d = gpu_u(n_err, re, s_oracle, prec) - u_ref
             short_err[prec] = {"max": float(np.abs(d).max() / 0.1), "rms": float(np.sqrt((d * d).mean()) / 0.1)}
         entry["error_vs_oracle"] = short_err
