@@ -96,13 +96,18 @@ __device__ __forceinline__ float warp_reduce_scatter32(float v[32], int lane)
 
 __device__ __forceinline__ float sigm(float v) { return 1.0f / (1.0f + expf(-v)); }
 
-template <int TN>
+// MT output tiles stacked along y share one halo window per 8-channel plane: (16 MT + 2) rows x 10
+// pixels x 16 B, and every stage's weights.
+template <int MT>
+constexpr int fwd_plane_bytes() { return (kTileRows * MT + 2) * kHaloPx * 16; }
+template <int MT>
+constexpr int fwd_a_bytes() { return (2 * fwd_plane_bytes<MT>() + 127) / 128 * 128; }   // 5,760 B for MT = 1
+template <int TN, int MT = 1>
 constexpr int fwd_stage_bytes()
 {
     // A: two planes (rounded up to 128 B); B: 18 slabs of TN rows x 16 B; rounded up to 1 KB
-    return ((2 * kPlane + 127) / 128 * 128 + 18 * TN * 16 + 1023) / 1024 * 1024;
+    return (fwd_a_bytes<MT>() + 18 * TN * 16 + 1023) / 1024 * 1024;
 }
-constexpr int kFwdA = (2 * kPlane + 127) / 128 * 128;      // 5,760 B
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -247,9 +252,11 @@ __device__ __forceinline__ void teardown(uint32_t tmem)
 }
 
 // ---- forward -------------------------------------------------------------------------------
-// grid (tiles in x, tiles in y, N * output-channel blocks); wp points at this launch's packed
-// weights: block nb, chunk i is the 18 * TN * 8 halves at ((nb * nchunks + i) * 18 * TN * 8).
-template <int TN>
+// grid (tiles in x, groups of MT tiles in y, N * output-channel blocks); wp points at this launch's
+// packed weights: block nb, chunk i is the 18 * TN * 8 halves at ((nb * nchunks + i) * 18 * TN * 8).
+// MT = 2: the CTA computes two 16 x 8 tiles stacked along y (accumulators at TMEM columns 0 and TN)
+// from one 34-row halo window, so each stage's weights serve twice the pixels.
+template <int TN, int MT>
 __global__ void __launch_bounds__(128)
 conv3_tma_kernel(const __grid_constant__ CUtensorMap tmx, const __half *__restrict__ wp, int H, int W, int C,
                  int cout, int ntn, int nstages, float alpha, float beta, float *y, int ldy, int vec_y, int *err,
@@ -262,15 +269,17 @@ conv3_tma_kernel(const __grid_constant__ CUtensorMap tmx, const __half *__restri
     __shared__ float sdb[TN];                                   // on == 2: this tile's bias-gradient sums
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int x0 = blockIdx.x * kTilePx, y0 = blockIdx.y * kTileRows;
+    const int x0 = blockIdx.x * kTilePx, y0 = blockIdx.y * kTileRows * MT;
     if (epi.on == 2 && threadIdx.x < TN) sdb[threadIdx.x] = 0.0f;
     const int img = blockIdx.z / ntn, nb = blockIdx.z % ntn, n0 = nb * TN;
     const int nchunks = C / kChunk;
-    constexpr int kSB = fwd_stage_bytes<TN>();
-    constexpr uint32_t kTx = 2 * kPlane + 18 * TN * 16;       // bytes the two copies of a stage bring
+    constexpr int kSB = fwd_stage_bytes<TN, MT>();
+    constexpr int kPl = fwd_plane_bytes<MT>();
+    constexpr int kA = fwd_a_bytes<MT>();
+    constexpr uint32_t kTx = 2 * kPl + 18 * TN * 16;          // bytes the two copies of a stage bring
     const uint32_t base = (smem_u32(dyn_raw) + 1023u) & ~1023u;
 
-    const uint32_t tmem = setup<TN>(&tmem_holder, full, empty, &done, nstages, &failed);
+    const uint32_t tmem = setup<TN * MT>(&tmem_holder, full, empty, &done, nstages, &failed);
 
     if (warp == 0 && lane == 0) {
         asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&tmx)) : "memory");
@@ -284,7 +293,7 @@ conv3_tma_kernel(const __grid_constant__ CUtensorMap tmx, const __half *__restri
             const uint32_t st = base + (uint32_t)(s * kSB), fb = smem_u32(&full[s]);
             expect_tx(fb, kTx);
             tma_load_4d(st, &tmx, 8 * (x0 - 1), y0 - 1, 2 * i, img, fb);       // planes 2i, 2i + 1
-            bulk_load(st + kFwdA, wblk + (size_t)i * 18 * TN * 8, 18 * TN * 16, fb);
+            bulk_load(st + kA, wblk + (size_t)i * 18 * TN * 8, 18 * TN * 16, fb);
         }
     } else if (warp == 1 && lane == 0) {
         for (int i = 0; i < nchunks; ++i) {
@@ -293,11 +302,14 @@ conv3_tma_kernel(const __grid_constant__ CUtensorMap tmx, const __half *__restri
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t st = base + (uint32_t)(s * kSB);
             #pragma unroll
-            for (int t = 0; t < 9; ++t) {
-                const int ky = t / 3, kx = t % 3;
-                mma_f16(tmem, desc(st + (uint32_t)((ky * kHaloPx + kx) * 16), kPlane, kHaloPx * 16),
-                        desc(st + kFwdA + (uint32_t)(2 * t * TN * 16), TN * 16, 128), idesc<TN, false>(),
-                        (i > 0 || t > 0) ? 1u : 0u);
+            for (int mt = 0; mt < MT; ++mt) {
+                #pragma unroll
+                for (int t = 0; t < 9; ++t) {
+                    const int ky = t / 3 + kTileRows * mt, kx = t % 3;
+                    mma_f16(tmem + (uint32_t)(mt * TN), desc(st + (uint32_t)((ky * kHaloPx + kx) * 16), kPl, kHaloPx * 16),
+                            desc(st + kA + (uint32_t)(2 * t * TN * 16), TN * 16, 128), idesc<TN, false>(),
+                            (i > 0 || t > 0) ? 1u : 0u);
+                }
             }
             commit(smem_u32(&empty[s]));
         }
@@ -308,16 +320,17 @@ conv3_tma_kernel(const __grid_constant__ CUtensorMap tmx, const __half *__restri
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
 
-    if (!failed) {
+    #pragma unroll 1
+    for (int mt = 0; mt < (failed ? 0 : MT); ++mt) {
         const int m = warp * 32 + lane;
-        const int yy = y0 + (m >> 3), xx = x0 + (m & 7);
+        const int yy = y0 + kTileRows * mt + (m >> 3), xx = x0 + (m & 7);
         const bool valid = yy < H && xx < W;
         const size_t pix = (size_t)((size_t)img * H + (valid ? yy : 0)) * W + (valid ? xx : 0);
         float *yrow = epi.on ? nullptr : y + pix * ldy;
         #pragma unroll 1
         for (int c = 0; c < TN; c += 32) {
             uint32_t r[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, r);
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mt * TN + c), r);
             const int col0 = n0 + c;
             if (epi.on == 2) {
                 float v[32];
@@ -410,12 +423,12 @@ conv3_tma_kernel(const __grid_constant__ CUtensorMap tmx, const __half *__restri
                 }
             }
         }
-        if (epi.on == 2 && epi.db) {
-            __syncthreads();                                    // every warp's sums are in sdb
-            if (threadIdx.x < TN && n0 + (int)threadIdx.x < cout) atomicAdd(epi.db + n0 + threadIdx.x, sdb[threadIdx.x]);
-        }
     }
-    teardown<TN>(tmem);
+    if (epi.on == 2 && epi.db && !failed) {
+        __syncthreads();                                        // every warp's sums are in sdb
+        if (threadIdx.x < TN && n0 + (int)threadIdx.x < cout) atomicAdd(epi.db + n0 + threadIdx.x, sdb[threadIdx.x]);
+    }
+    teardown<TN * MT>(tmem);
 }
 
 // ---- weight gradient -------------------------------------------------------------------------
@@ -794,32 +807,81 @@ bool blocked_args_ok(const void *p, int N, int H, int W, int C)
            (long long)N * H * W * C <= (1LL << 40) && (long long)W * 8 <= 0xffffffffLL;
 }
 
-template <int TN>
-cudaError_t launch_conv3_tma(const CUtensorMap &tmx, const __half *wp, int N, int H, int W, int C, int cout,
-                             float alpha, float beta, float *y, int ldy, int *err, cudaStream_t s, const Epi &epi,
-                             unsigned long long wait_ns = kWaitNs, int withhold = 0)
+// SMs of the current device (the grid-size heuristics below).
+int sm_count()
 {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+            n = 148;
+    }
+    return n;
+}
+
+// Stages a CTA reserves in shared memory: at least what its pipeline uses, and enough that the CTAs
+// resident on one SM (228 KB of shared memory, 1 KB of it reserved per CTA, plus the 1 KB alignment
+// slack of the dynamic allocation) fit their accumulators in the 512 TMEM columns.
+int reserve_stages(int nstages, int stage_bytes, int tmem_cols)
+{
+    const int max_ctas = 512 / tmem_cols;
+    int r = nstages;
+    while ((long long)(r * stage_bytes + 2048) * (max_ctas + 1) <= 233472) ++r;
+    return r;
+}
+
+template <int TN, int MT>
+cudaError_t launch_conv3_tma_mt(const void *xb, const __half *wp, int N, int H, int W, int C, int cout, float alpha,
+                                float beta, float *y, int ldy, int *err, cudaStream_t s, const Epi &epi,
+                                unsigned long long wait_ns, int withhold, CUresult *map_err)
+{
+    CUtensorMap tmx;
+    *map_err = blocked_map(&tmx, xb, N, H, W, C, kHaloPx, kTileRows * MT + 2, 2);
+    if (*map_err != CUDA_SUCCESS) return cudaErrorInvalidValue;
     const int ntn = (cout + TN - 1) / TN;
     const int nchunks = C / kChunk;
-    // a 32-wide tile with at most two chunks: one stage (15 KB), so that 14 CTAs share an SM and
+    // a 32-wide single tile with at most two chunks: one stage (15 KB), so that 14 CTAs share an SM and
     // hide each other's copy latency; otherwise up to four stages per CTA
-    const int nstages = (TN == 32 && nchunks <= 2) ? 1 : (nchunks < kFwdStages ? nchunks : kFwdStages);
-    // shared memory also caps the CTAs per SM so that their accumulators fit in the 512 TMEM
-    // columns: with 128 columns each, at most 4 CTAs may be resident, so reserve >= 2 stages
-    const int reserve = (TN == 128 && nstages < 2) ? 2 : nstages;
-    const size_t smem = (size_t)reserve * fwd_stage_bytes<TN>() + 1024;
-    dim3 grid((W + kTilePx - 1) / kTilePx, (H + kTileRows - 1) / kTileRows, N * ntn);
+    const int nstages = (TN == 32 && MT == 1 && nchunks <= 2) ? 1 : (nchunks < kFwdStages ? nchunks : kFwdStages);
+    const int reserve = reserve_stages(nstages, fwd_stage_bytes<TN, MT>(), TN * MT);
+    const size_t smem = (size_t)reserve * fwd_stage_bytes<TN, MT>() + 1024;
+    dim3 grid((W + kTilePx - 1) / kTilePx, (H + kTileRows * MT - 1) / (kTileRows * MT), N * ntn);
     const int vec_y = (ldy % 4 == 0) && ((reinterpret_cast<uintptr_t>(y) & 15) == 0);
     static bool attr_set = false;       // per instantiation
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(conv3_tma_kernel<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(kFwdStages * fwd_stage_bytes<TN>() + 1024));
+        const int most = (kFwdStages > reserve ? kFwdStages : reserve) * fwd_stage_bytes<TN, MT>() + 1024;
+        cudaError_t e = cudaFuncSetAttribute(conv3_tma_kernel<TN, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             most > 232448 ? 232448 : most);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    conv3_tma_kernel<TN><<<grid, 128, smem, s>>>(tmx, wp, H, W, C, cout, ntn, nstages, alpha, beta, y, ldy, vec_y,
-                                                 err, epi, wait_ns, withhold);
+    conv3_tma_kernel<TN, MT><<<grid, 128, smem, s>>>(tmx, wp, H, W, C, cout, ntn, nstages, alpha, beta, y, ldy,
+                                                     vec_y, err, epi, wait_ns, withhold);
     return cudaGetLastError();
+}
+
+// Two stacked tiles per CTA halve the weight traffic per pixel.  They are used for 128-wide output tiles
+// (weights are 36 of a stage's 42 KB) unless the coarser grid leaves SMs idle: a pair costs about 1.6
+// single tiles (measured on 64 x 64 and 32 x 32 layers at batch 16), so pairs are taken when
+// 1.6 ceil(pairs / SMs) <= ceil(tiles / SMs).  Pairs of 64-wide tiles measured 10-20% slower than
+// single tiles and are not used.
+template <int TN>
+cudaError_t launch_conv3_tma(const void *xb, const __half *wp, int N, int H, int W, int C, int cout, float alpha,
+                             float beta, float *y, int ldy, int *err, cudaStream_t s, const Epi &epi,
+                             CUresult *map_err, unsigned long long wait_ns = kWaitNs, int withhold = 0)
+{
+    if constexpr (TN == 128) {
+        const long long cols = (long long)((W + kTilePx - 1) / kTilePx) * N * ((cout + TN - 1) / TN);
+        const long long tiles = cols * ((H + kTileRows - 1) / kTileRows);
+        const long long pairs = cols * ((H + 2 * kTileRows - 1) / (2 * kTileRows));
+        const int sms = sm_count();
+        if (8 * ((pairs + sms - 1) / sms) <= 5 * ((tiles + sms - 1) / sms))
+            return launch_conv3_tma_mt<TN, 2>(xb, wp, N, H, W, C, cout, alpha, beta, y, ldy, err, s, epi, wait_ns,
+                                              withhold, map_err);
+    }
+    return launch_conv3_tma_mt<TN, 1>(xb, wp, N, H, W, C, cout, alpha, beta, y, ldy, err, s, epi, wait_ns, withhold,
+                                      map_err);
 }
 
 } // namespace
@@ -946,20 +1008,19 @@ int conv3_tma_run(const char *name, const void *xb, int N, int H, int W, int C, 
         return tma_fail(SMRT_ERR_ARG,
                         "%s: bad arguments (N %d H %d W %d C %d cout %d ldy %d; C must be a multiple "
                         "of 16, xb and wp 16-byte aligned)", name, N, H, W, C, cout, ldy);
-    CUtensorMap tmx;
-    CUresult r = blocked_map(&tmx, xb, N, H, W, C, kHaloPx, kHaloRows, 2);
-    if (r != CUDA_SUCCESS) return tma_fail(SMRT_ERR_CUDA, "%s: tensor map rejected (%d)", name, (int)r);
     cudaStream_t s = (cudaStream_t)stream;
     const __half *w = (const __half *)wp;
     cudaError_t e;
+    CUresult r = CUDA_SUCCESS;
     const int TN = tile_n(cout);
     const Epi plain{nullptr, nullptr, nullptr, nullptr, 0, 0, nullptr, nullptr};
     if (TN == 32)
-        e = launch_conv3_tma<32>(tmx, w, N, H, W, C, cout, alpha, beta, y, ldy, err, s, plain, wait_ns, withhold);
+        e = launch_conv3_tma<32>(xb, w, N, H, W, C, cout, alpha, beta, y, ldy, err, s, plain, &r, wait_ns, withhold);
     else if (TN == 64)
-        e = launch_conv3_tma<64>(tmx, w, N, H, W, C, cout, alpha, beta, y, ldy, err, s, plain, wait_ns, withhold);
+        e = launch_conv3_tma<64>(xb, w, N, H, W, C, cout, alpha, beta, y, ldy, err, s, plain, &r, wait_ns, withhold);
     else
-        e = launch_conv3_tma<128>(tmx, w, N, H, W, C, cout, alpha, beta, y, ldy, err, s, plain, wait_ns, withhold);
+        e = launch_conv3_tma<128>(xb, w, N, H, W, C, cout, alpha, beta, y, ldy, err, s, plain, &r, wait_ns, withhold);
+    if (r != CUDA_SUCCESS) return tma_fail(SMRT_ERR_CUDA, "%s: tensor map rejected (%d)", name, (int)r);
     if (e != cudaSuccess) return tma_fail(SMRT_ERR_CUDA, "%s: %s", name, cudaGetErrorString(e));
     return SMRT_OK;
 }
@@ -1012,18 +1073,16 @@ extern "C" int smrt_nn_conv3_tma_bias_act(const void *xb, int N, int H, int W, i
         return tma_fail(SMRT_ERR_ARG,
                         "smrt_nn_conv3_tma_bias_act: bad arguments (N %d H %d W %d C %d cout %d; C %% 16 == 0, "
                         "cout %% 8 == 0, 16-byte aligned outputs, at least one output)", N, H, W, C, cout);
-    CUtensorMap tmx;
-    CUresult r = blocked_map(&tmx, xb, N, H, W, C, kHaloPx, kHaloRows, 2);
-    if (r != CUDA_SUCCESS)
-        return tma_fail(SMRT_ERR_CUDA, "smrt_nn_conv3_tma_bias_act: tensor map rejected (%d)", (int)r);
     cudaStream_t s = (cudaStream_t)stream;
+    CUresult r = CUDA_SUCCESS;
     const __half *w = (const __half *)wp;
     const Epi epi{bias, z, a, (__half *)ab, act, 1, nullptr, nullptr};
     cudaError_t e;
     const int TN = tile_n(cout);
-    if (TN == 32) e = launch_conv3_tma<32>(tmx, w, N, H, W, C, cout, 1.0f, 0.0f, nullptr, cout, err, s, epi);
-    else if (TN == 64) e = launch_conv3_tma<64>(tmx, w, N, H, W, C, cout, 1.0f, 0.0f, nullptr, cout, err, s, epi);
-    else e = launch_conv3_tma<128>(tmx, w, N, H, W, C, cout, 1.0f, 0.0f, nullptr, cout, err, s, epi);
+    if (TN == 32) e = launch_conv3_tma<32>(xb, w, N, H, W, C, cout, 1.0f, 0.0f, nullptr, cout, err, s, epi, &r);
+    else if (TN == 64) e = launch_conv3_tma<64>(xb, w, N, H, W, C, cout, 1.0f, 0.0f, nullptr, cout, err, s, epi, &r);
+    else e = launch_conv3_tma<128>(xb, w, N, H, W, C, cout, 1.0f, 0.0f, nullptr, cout, err, s, epi, &r);
+    if (r != CUDA_SUCCESS) return tma_fail(SMRT_ERR_CUDA, "smrt_nn_conv3_tma_bias_act: tensor map rejected (%d)", (int)r);
     if (e != cudaSuccess) return tma_fail(SMRT_ERR_CUDA, "smrt_nn_conv3_tma_bias_act: %s", cudaGetErrorString(e));
     return SMRT_OK;
 }
@@ -1040,18 +1099,16 @@ extern "C" int smrt_nn_conv3_tma_act_bwd(const void *dzb, int N, int H, int W, i
         return tma_fail(SMRT_ERR_ARG,
                         "smrt_nn_conv3_tma_act_bwd: bad arguments (N %d H %d W %d C %d cout %d; C %% 16 == 0, "
                         "cout %% 8 == 0, 16-byte aligned z, dz, dzb_out)", N, H, W, C, cout);
-    CUtensorMap tmx;
-    CUresult r = blocked_map(&tmx, dzb, N, H, W, C, kHaloPx, kHaloRows, 2);
-    if (r != CUDA_SUCCESS)
-        return tma_fail(SMRT_ERR_CUDA, "smrt_nn_conv3_tma_act_bwd: tensor map rejected (%d)", (int)r);
     cudaStream_t s = (cudaStream_t)stream;
+    CUresult r = CUDA_SUCCESS;
     const __half *w = (const __half *)wp;
     const Epi epi{nullptr, dz, nullptr, (__half *)dzb_out, act, 2, z, db};
     cudaError_t e;
     const int TN = tile_n(cout);
-    if (TN == 32) e = launch_conv3_tma<32>(tmx, w, N, H, W, C, cout, 1.0f, 0.0f, nullptr, cout, err, s, epi);
-    else if (TN == 64) e = launch_conv3_tma<64>(tmx, w, N, H, W, C, cout, 1.0f, 0.0f, nullptr, cout, err, s, epi);
-    else e = launch_conv3_tma<128>(tmx, w, N, H, W, C, cout, 1.0f, 0.0f, nullptr, cout, err, s, epi);
+    if (TN == 32) e = launch_conv3_tma<32>(dzb, w, N, H, W, C, cout, 1.0f, 0.0f, nullptr, cout, err, s, epi, &r);
+    else if (TN == 64) e = launch_conv3_tma<64>(dzb, w, N, H, W, C, cout, 1.0f, 0.0f, nullptr, cout, err, s, epi, &r);
+    else e = launch_conv3_tma<128>(dzb, w, N, H, W, C, cout, 1.0f, 0.0f, nullptr, cout, err, s, epi, &r);
+    if (r != CUDA_SUCCESS) return tma_fail(SMRT_ERR_CUDA, "smrt_nn_conv3_tma_act_bwd: tensor map rejected (%d)", (int)r);
     if (e != cudaSuccess) return tma_fail(SMRT_ERR_CUDA, "smrt_nn_conv3_tma_act_bwd: %s", cudaGetErrorString(e));
     return SMRT_OK;
 }

@@ -104,6 +104,9 @@ def _conv(n, h, w, C, cout, alpha, beta, seed):
     (1, 16, 8, 80, 48),       # 5 chunks: the 4 stages are reused
     (1, 20, 12, 96, 130),     # two 128-wide output-channel tiles, the second partial
     (1, 24, 16, 384, 128),    # the widest decoder input (24 chunks)
+    (10, 70, 40, 32, 136),    # stacked tile pairs (300 CTAs), the last pair partly outside, two N tiles
+    (16, 48, 56, 80, 256),    # stacked pairs over 5 chunks (the stages are reused)
+    (16, 70, 44, 48, 48),     # a grid where pairs would apply, but 64-wide tiles run single
 ])
 def test_conv3_tma_matches_fp64_product_of_the_same_halves(n, h, w, C, cout):
     got, exp, err, _ = _conv(n, h, w, C, cout, 0.75, 0.5, seed=C * 1000 + cout)
@@ -245,7 +248,8 @@ def test_wait_timeout_is_reported_and_the_next_call_runs():
 
 
 @pytest.mark.parametrize("act", [1, 0])
-@pytest.mark.parametrize("n,h,w,C,cout", [(2, 37, 21, 32, 16), (1, 32, 40, 64, 32), (2, 18, 10, 32, 136)])
+@pytest.mark.parametrize("n,h,w,C,cout", [(2, 37, 21, 32, 16), (1, 32, 40, 64, 32), (2, 18, 10, 32, 136),
+                                         (10, 70, 40, 32, 136), (16, 70, 44, 48, 48)])
 def test_conv3_tma_act_bwd_equals_the_unfused_pair(n, h, w, C, cout, act):
     """The input gradient with the SiLU backward of the producing layer in its epilogue gives exactly the
     blocked halves and float32 dz that smrt_nn_conv3_tma followed by smrt_nn_bias_act_bwd_blocked give,
