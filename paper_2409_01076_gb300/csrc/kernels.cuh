@@ -577,11 +577,26 @@ __global__ void macros_kernel(const typename Prec<PREC>::R *state, double *rho, 
 }
 
 // ---- residual: u(t) and u(t+1) without advancing the state ------------------------
-// A block takes 32 x 8 tiles; for the tile plus a one-node halo it pulls f(t),
-// collides (the same code as the step) and keeps f* (rounded to the storage
-// format, as the step stores it) in shared memory; each tile node then pulls
-// f(t+1) from there.  Sums in double: |u1-u0|^2, |u1|^2, rho0, rho0 ux0, rho0 uy0.
+// kRTX x kRTY tiles: the layout of the caller-scratch residual (smrt_residual_noalloc).
 constexpr int kRTX = 32, kRTY = 8, kRHX = kRTX + 2, kRHY = kRTY + 2;
+
+// The handle's residual sweeps rows.  A warp owns a strip of kRSW = 30 columns (lanes 1..30; lanes 0
+// and 31 are the neighbouring columns, wrapped where the x axis is periodic) and a segment of kRSR
+// rows, and walks it from the row below to the row above.  For each row every lane pulls f(t) of its
+// node, collides it (the code of the step) and rounds f* to the storage format as the step stores
+// it; f(t+1) of a node on the previous row then comes from registers: the populations arriving along
+// x from the neighbouring lanes by warp shuffles, those arriving along y from the rows kept before
+// and after it, and bounce-back terms from the node's own f*.  Collisions per node: 32/30 x
+// (kRSR + 2)/kRSR; no shared memory, no block barrier.  Sums: |u1-u0|^2, |u1|^2, rho0, rho0 ux0,
+// rho0 uy0.
+// Double offsets: u0 and u1 by moments_d and their difference.  Float offsets (the 32- and 16-bit
+// formats): the change is formed from the offset differences in float,
+//   u1 - u0 = (dj - u0 drho) / rho1,  drho = sum_a (g1_a - g0_a),  dj = sum_a c_a (g1_a - g0_a),
+// which is u1 - u0 without the cancellation of two nearly equal velocities (relative error ~1e-6 of
+// the change itself); rho0 - 1 and j0 = rho0 u0 are float sums of the offsets.  A thread adds its
+// nodes' terms into compensated float pairs (value + rounding error, ~48 significant bits); the
+// warp, block and grid sums of those are in double.
+constexpr int kRSW = 30, kRSR = 64;
 
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -590,77 +605,169 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-template <int PREC, int KIND, int MODE, bool SR = false>
-__global__ void __launch_bounds__(256)
-residual_kernel(const typename Prec<PREC>::R *state, const Params<typename Prec<PREC>::C> p,
-                double *partials, int tiles_x, int tiles_y)
+// pull_canonical for a node whose nine source nodes lie inside the lattice (no wall, no wrap).
+template <int PREC, int MODE>
+__device__ __forceinline__ void pull_inner(const typename Prec<PREC>::R *state, const Params<typename Prec<PREC>::C> &p,
+                                           int i, int j, typename Prec<PREC>::C g[9])
 {
     using P = Prec<PREC>;
-    using R = typename P::R;
+    const typename P::R *s0 = state + (size_t)j * (size_t)p.pitch + (size_t)i;
+    #pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        const long long off = (MODE == MODE_AA_EVEN) ? (long long)a * p.plane
+                              : (long long)(MODE == MODE_AB ? a : opp(a)) * p.plane -
+                                    (long long)ey(a) * p.pitch - ex(a);
+        g[a] = P::to_c(s0[off]);
+    }
+}
+
+// f(t) of node (i, j) of the sweep, wrapped onto the lattice; false where (i, j) is behind a wall or
+// beyond the lattice (no node).  (i, j) are updated to the wrapped node.
+template <int PREC, int MODE>
+__device__ __forceinline__ bool sweep_pull(const typename Prec<PREC>::R *state, const Params<typename Prec<PREC>::C> &p,
+                                           int &i, int &j, typename Prec<PREC>::C g[9])
+{
+    if (i > p.nx || j > p.ny) return false;
+    if (resolve(p, i, j) >= 0) return false;
+    if (i >= 1 && i + 1 < p.nx && j >= 1 && j + 1 < p.ny) pull_inner<PREC, MODE>(state, p, i, j, g);
+    else pull_canonical<PREC, MODE>(state, p, i, j, g);
+    return true;
+}
+
+#ifndef SMRT_RESID_MIN_BLOCKS
+#define SMRT_RESID_MIN_BLOCKS 3          // blocks per SM the register budget is set for (sweepable)
+#endif
+
+template <int PREC, int KIND, int MODE, bool SR = false>
+__global__ void __launch_bounds__(256, SMRT_RESID_MIN_BLOCKS)
+residual_kernel(const typename Prec<PREC>::R *__restrict__ state, const Params<typename Prec<PREC>::C> p,
+                double *partials, int strips, int segs)
+{
+    using P = Prec<PREC>;
     using C = typename P::C;
-    __shared__ R post[9][kRHY][kRHX];
-    __shared__ double u0s[3][kRTY][kRTX];
+    constexpr bool kFloat = sizeof(C) == 4;
     __shared__ double red[8][kResidualSums];
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     double acc[kResidualSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    const int ntiles = tiles_x * tiles_y;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int tx0 = (tile % tiles_x) * kRTX, ty0 = (tile / tiles_x) * kRTY;
-        for (int q = tid; q < kRHX * kRHY; q += 256) {
-            const int hx = q % kRHX, hy = q / kRHX;
-            int i = tx0 - 1 + hx, j = ty0 - 1 + hy;
-            const bool tile_node = hx >= 1 && hx <= kRTX && hy >= 1 && hy <= kRTY && i < p.nx && j < p.ny;
-            if (i > p.nx || j > p.ny) continue;
-            if (resolve(p, i, j) >= 0) continue;
-            C g[9];
-            pull_canonical<PREC, MODE>(state, p, i, j, g);
-            if (tile_node) {
-                double rr, ux, uy;
-                moments_any(g, rr, ux, uy);
-                u0s[0][hy - 1][hx - 1] = rr;
-                u0s[1][hy - 1][hx - 1] = ux;
-                u0s[2][hy - 1][hx - 1] = uy;
-            }
-            collide<KIND, Prec<PREC>::kExactWeights>(p, g);
-            const uint32_t nh = SR ? sr_node_hash((uint32_t)j * (uint32_t)p.nx + (uint32_t)i, p.salt) : 0u;
+    float cs[kResidualSums] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, cc[kResidualSums] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    int nodes = 0;
+    const long long items = (long long)strips * segs;
+    for (long long item = (long long)blockIdx.x * 8 + (tid >> 5); item < items; item += (long long)gridDim.x * 8) {
+        const int x0 = (int)(item % strips) * kRSW, r0 = (int)(item / strips) * kRSR;
+        const int rows = min(kRSR, p.ny - r0);
+        const int i = x0 - 1 + lane;                            // this lane's column
+        const bool own_col = lane >= 1 && lane <= kRSW && i < p.nx;
+        // row j - 1 (f* of this lane, shuffled arrivals, f(t)) and row j - 2 (the y-arrivals)
+        C own1[9], g01[9];
+        C in1_1 = 0, in3_1 = 0, in5_1 = 0, in6_1 = 0;          // f*_1, f*_3, f*_5, f*_6 from lanes -1/+1/-1/+1
+        C own2_2 = 0, in5_2 = 0, in6_2 = 0;
+        #pragma unroll
+        for (int a = 0; a < 9; ++a) own1[a] = g01[a] = 0;
+        #pragma unroll 1
+        for (int jj = -1; jj <= rows; ++jj) {
+            int wi = i, wj = r0 + jj;
+            C g[9], pc[9];
             #pragma unroll
-            for (int a = 0; a < 9; ++a) post[a][hy][hx] = round_store<PREC, SR>(g[a], nh, a);
-        }
-        __syncthreads();
-        const int lx = tid % kRTX, ly = tid / kRTX;
-        const int i = tx0 + lx, j = ty0 + ly;
-        if (i < p.nx && j < p.ny) {
-            C g1[9];
+            for (int a = 0; a < 9; ++a) g[a] = pc[a] = 0;
+            if (sweep_pull<PREC, MODE>(state, p, wi, wj, g)) {
+                #pragma unroll
+                for (int a = 0; a < 9; ++a) pc[a] = g[a];
+                collide<KIND, Prec<PREC>::kExactWeights>(p, pc);
+                const uint32_t nh = SR ? sr_node_hash((uint32_t)wj * (uint32_t)p.nx + (uint32_t)wi, p.salt) : 0u;
+                #pragma unroll
+                for (int a = 0; a < 9; ++a) pc[a] = P::to_c(round_store<PREC, SR>(pc[a], nh, a));
+            }
+            // arrivals along x: ex = +1 populations from lane - 1, ex = -1 from lane + 1
+            const C up1 = __shfl_up_sync(kFull, pc[1], 1), up5 = __shfl_up_sync(kFull, pc[5], 1),
+                    up8 = __shfl_up_sync(kFull, pc[8], 1);
+            const C dn3 = __shfl_down_sync(kFull, pc[3], 1), dn6 = __shfl_down_sync(kFull, pc[6], 1),
+                    dn7 = __shfl_down_sync(kFull, pc[7], 1);
+            if (jj >= 1 && own_col) {
+                // f(t+1) of node (i, r0 + jj - 1)
+                const int jn = r0 + jj - 1;
+                C g1[9];
+                g1[0] = own1[0];
+                g1[1] = in1_1;
+                g1[3] = in3_1;
+                g1[2] = own2_2;
+                g1[5] = in5_2;
+                g1[6] = in6_2;
+                g1[4] = pc[4];
+                g1[7] = dn7;
+                g1[8] = up8;
+                if (i == 0 || i + 1 == p.nx || jn == 0 || jn + 1 == p.ny) {
+                    #pragma unroll
+                    for (int a = 1; a < 9; ++a) {
+                        int si = i - ex(a), sj = jn - ey(a);
+                        const int side = resolve(p, si, sj);
+                        if (side >= 0) g1[a] = own1[opp(a)] + p.corr[side][a];
+                    }
+                }
+                if constexpr (kFloat) {
+                    float d[9];
+                    #pragma unroll
+                    for (int a = 0; a < 9; ++a) d[a] = g1[a] - g01[a];
+                    const float rho0m1 = (((g01[0] + g01[1]) + (g01[2] + g01[3])) +
+                                          ((g01[4] + g01[5]) + (g01[6] + g01[7]))) + g01[8];
+                    const float jx0 = ((g01[1] - g01[3]) + (g01[5] - g01[6])) + (g01[8] - g01[7]);
+                    const float jy0 = ((g01[2] - g01[4]) + (g01[5] - g01[7])) + (g01[6] - g01[8]);
+                    const float drho = (((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7]))) + d[8];
+                    const float djx = ((d[1] - d[3]) + (d[5] - d[6])) + (d[8] - d[7]);
+                    const float djy = ((d[2] - d[4]) + (d[5] - d[7])) + (d[6] - d[8]);
+                    const float rho0 = 1.0f + rho0m1;
+                    const float inv0 = 1.0f / rho0, inv1 = 1.0f / (rho0 + drho);
+                    const float ux0 = jx0 * inv0, uy0 = jy0 * inv0;
+                    const float dx = (djx - ux0 * drho) * inv1, dy = (djy - uy0 * drho) * inv1;
+                    const float ux1 = ux0 + dx, uy1 = uy0 + dy;
+                    two_sum_acc(cs[0], cc[0], dx * dx + dy * dy);
+                    two_sum_acc(cs[1], cc[1], ux1 * ux1 + uy1 * uy1);
+                    two_sum_acc(cs[2], cc[2], rho0m1);
+                    two_sum_acc(cs[3], cc[3], jx0);
+                    two_sum_acc(cs[4], cc[4], jy0);
+                    ++nodes;
+                } else {
+                    double r0d, ux0, uy0, r1, ux1, uy1;
+                    moments_any(g01, r0d, ux0, uy0);
+                    moments_any(g1, r1, ux1, uy1);
+                    const double dx = ux1 - ux0, dy = uy1 - uy0;
+                    acc[0] += dx * dx + dy * dy;
+                    acc[1] += ux1 * ux1 + uy1 * uy1;
+                    acc[2] += r0d;
+                    acc[3] += r0d * ux0;
+                    acc[4] += r0d * uy0;
+                }
+            }
+            // shift: row j - 1 becomes row j - 2, row j becomes row j - 1
+            own2_2 = own1[2];
+            in5_2 = in5_1;
+            in6_2 = in6_1;
             #pragma unroll
             for (int a = 0; a < 9; ++a) {
-                int si = i - ex(a), sj = j - ey(a);
-                int side = resolve(p, si, sj);
-                if (side >= 0) g1[a] = P::to_c(post[opp(a)][ly + 1][lx + 1]) + p.corr[side][a];
-                else g1[a] = P::to_c(post[a][ly + 1 - ey(a)][lx + 1 - ex(a)]);
+                own1[a] = pc[a];
+                g01[a] = g[a];
             }
-            double r1, ux1, uy1;
-            moments_any(g1, r1, ux1, uy1);
-            const double r0 = u0s[0][ly][lx], ux0 = u0s[1][ly][lx], uy0 = u0s[2][ly][lx];
-            const double dx = ux1 - ux0, dy = uy1 - uy0;
-            acc[0] += dx * dx + dy * dy;
-            acc[1] += ux1 * ux1 + uy1 * uy1;
-            acc[2] += r0;
-            acc[3] += r0 * ux0;
-            acc[4] += r0 * uy0;
+            in1_1 = up1;
+            in3_1 = dn3;
+            in5_1 = up5;
+            in6_1 = dn6;
         }
-        __syncthreads();
+    }
+    if constexpr (kFloat) {
+        #pragma unroll
+        for (int k = 0; k < kResidualSums; ++k) acc[k] = (double)cs[k] + (double)cc[k];
+        acc[2] += (double)nodes;
     }
     #pragma unroll
     for (int k = 0; k < kResidualSums; ++k) acc[k] = warp_sum(acc[k]);
-    if ((tid & 31) == 0) {
+    if (lane == 0) {
         #pragma unroll
         for (int k = 0; k < kResidualSums; ++k) red[tid >> 5][k] = acc[k];
     }
     __syncthreads();
     if (tid < kResidualSums) {
-        double s = 0.0;
-        for (int w = 0; w < 8; ++w) s += red[w][tid];
-        partials[(size_t)blockIdx.x * kResidualSums + tid] = s;
+        double sum = 0.0;
+        for (int w = 0; w < 8; ++w) sum += red[w][tid];
+        partials[(size_t)blockIdx.x * kResidualSums + tid] = sum;
     }
 }
 
@@ -826,20 +933,21 @@ cudaError_t launch_residual_k(int mode, const void *state, const HostParams &hp,
 {
     using P = Prec<PREC>;
     const Params<typename P::C> p = make_params<typename P::C>(hp);
-    const int tiles_x = (hp.nx + kRTX - 1) / kRTX, tiles_y = (hp.ny + kRTY - 1) / kRTY;
-    long long nt = (long long)tiles_x * tiles_y;
-    const int nb = (int)(nt < kResidualMaxBlocks ? nt : kResidualMaxBlocks);
+    const int strips = (hp.nx + kRSW - 1) / kRSW, segs = (hp.ny + kRSR - 1) / kRSR;
+    const long long warps = (long long)strips * segs;
+    const long long want = (warps + 7) / 8;
+    const int nb = (int)(want < kResidualMaxBlocks ? want : kResidualMaxBlocks);
     bool plain = true;
     if constexpr (PREC == SMRT_PREC_F16 || PREC == SMRT_PREC_BF16) {
         if (hp.rounding == SMRT_ROUND_STOCHASTIC) {
             plain = false;
             SMRT_MODE_SWITCH(mode, (residual_kernel<PREC, KIND, M, true><<<nb, 256, 0, s>>>(
-                                       (const typename P::R *)state, p, sc.partials, tiles_x, tiles_y)));
+                                       (const typename P::R *)state, p, sc.partials, strips, segs)));
         }
     }
     if (plain) {
         SMRT_MODE_SWITCH(mode, (residual_kernel<PREC, KIND, M><<<nb, 256, 0, s>>>((const typename P::R *)state, p,
-                                                                                     sc.partials, tiles_x, tiles_y)));
+                                                                                     sc.partials, strips, segs)));
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -88,7 +88,9 @@ def test_sr_is_reproducible_and_resumes_from_a_checkpoint(prec, tmp_path):
 @pytest.mark.parametrize("layout", ["ab", "aa"])
 def test_sr_residual_sees_the_state_the_next_step_stores(prec, layout):
     """smrt_residual rounds u(t+1) itself; with stochastic rounding it must draw the bits the step
-    draws.  Recompute r from the moments before and after one real step."""
+    draws.  Recompute r from the moments before and after one real step.  The float formats form the
+    change from offset differences in float (1e-5 relative covers its roundings); bits drawn for another
+    (node, population, t) would move r by several per cent here."""
     nx, ny, tau, U = 70, 44, 0.58, 0.1
     h = _sr(make(nx, ny, tau, U, W.CAVITY, prec=prec, layout=layout))
     S.smrt_step(h, 41)
@@ -97,7 +99,7 @@ def test_sr_residual_sees_the_state_the_next_step_stores(prec, layout):
     S.smrt_step(h, 1)
     _, u1 = get_macros(h)
     r_ref = np.sqrt(((u1 - u0) ** 2).sum()) / np.sqrt((u1 ** 2).sum())
-    assert abs(r - r_ref) <= 1e-9 * r_ref, (r, r_ref)
+    assert abs(r - r_ref) <= 1e-5 * r_ref, (r, r_ref)
     S.smrt_destroy(h)
 
 
