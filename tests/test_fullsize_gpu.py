@@ -61,6 +61,37 @@ def test_tgv_8192_windows(layout, kind):
     torch.cuda.empty_cache()
 
 
+@pytest.mark.parametrize("prec,layout", [("f32", "ab"), ("f16", "aa")])
+def test_tgv_16384_windows_past_2_31_elements(prec, layout):
+    """A 16384^2 lattice: one buffer holds 9 x 2^28 = 2.4e9 elements, past 2^31, so the plane offsets
+    of the upper populations and every pull and push address there need 64-bit arithmetic.  Windows
+    at the corners and deep in the plane against the oracle; the residual's mass sum at full size."""
+    import torch
+    n, u0, tau, s, Wd = 16384, 0.05, 0.51, 6, 16
+    h = make(n, n, tau, 0.0, W.ALL_PERIODIC, prec=prec, layout=layout)
+    rho, u = W.tgv_fields(n, n, u0)
+    S.smrt_init_macros(h, torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
+    del rho, u
+    S.smrt_step(h, s)
+    fd = _gpu_f_device(h)
+    for x0, y0 in [(0, 0), (n - Wd, n - Wd), (9000, 15000), (16000, 5)]:
+        r, uu = W.tgv_fields(n, n, u0, x0 - s, y0 - s, Wd + 2 * s, Wd + 2 * s)
+        ref = O.run(O.init_equilibrium(r, uu), s, O.ALL_PERIODIC, tau)[:, s:s + Wd, s:s + Wd]
+        if prec == "f32":
+            _compare_window(fd, ref, x0, y0, Wd, u0)
+        else:
+            # 16-bit offsets: six roundings of each population (~1.5e-5 each); an addressing error
+            # would be of the order of the populations themselves
+            got = fd[:, y0:y0 + Wd, x0:x0 + Wd].cpu().numpy()
+            assert np.abs(got - ref).max() <= 5e-4, (x0, y0)
+            assert np.abs(O.macros(got)[1] - O.macros(ref)[1]).max() <= 1e-2 * u0, (x0, y0)
+    _, sums = S.smrt_residual(h)
+    assert abs(sums[0] / (n * n) - 1.0) < 1e-6
+    del fd
+    S.smrt_destroy(h)
+    torch.cuda.empty_cache()
+
+
 @pytest.mark.parametrize("layout", ["ab", "aa"])
 def test_cavity_4096_re10000_windows(layout):
     import torch
