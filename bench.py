@@ -55,7 +55,7 @@ def parse_args(argv=None):
     p.add_argument("--no-learned", action="store_true",
                    help="leave the learned warm-start leg (training + time to steady at the same error) out")
     p.add_argument("--learned-count", type=int, default=2000)
-    p.add_argument("--learned-iters", type=int, default=2000)
+    p.add_argument("--learned-iters", type=int, default=12000)
     p.add_argument("--learned-cap", type=int, default=150000)
     p.add_argument("--learned-cap-1024", type=int, default=1000000)
     p.add_argument("--batch-count", type=int, default=512)

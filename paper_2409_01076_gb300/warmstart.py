@@ -78,7 +78,10 @@ def train(net, res, targets, iters: int = 2000, batch: int = 16, lr: float = 1e-
     Measured on 256 solver-generated 256^2 cavities (800 iterations, two seeds, both GEMM
     backends): a peak rate of 1e-3 reaches a held-out MSE of 0.7-1.3e-4 in every run, with or
     without the warm-up; 2e-3 is unstable (loss spikes when the rate peaks, stalls near the
-    mean-field loss in some runs).
+    mean-field loss in some runs).  On 2,000 cavities the held-out error keeps falling with the
+    length of the schedule: max |u - u_steady| / U over nine steady cavities (Re 130-2,500) of
+    0.08-0.15 after 2,000 iterations, 0.024-0.032 after 6,000 and 0.010-0.017 after 12,000 (rms
+    2.5e-3 -> 1.0e-3 -> 5e-4 at Re <= 1,200); 7e-4 instead of 1e-3 at 6,000 was worse.
 
     graph: the forward and backward pass is recorded once as a CUDA graph (UNet.capture) and
     replayed on static input tensors that each iteration's batch is copied into; Adam runs outside
@@ -252,11 +255,18 @@ def time_to_same_error(net, res, n: int, prec: int = None, tol: float = 1e-7, re
     level -- and in FP32 each run also freezes at its own fixed point once every correction rounds
     away.  Wall times are steps x the measured per-update time of the lattice (CUDA events over the
     update launches); the warm time adds the prediction (network, resampling, smrt_init_macros).
-    A run that does not reach `tol` within max_steps is reported as capped and left out."""
+    A run that does not reach `tol` within max_steps is reported as capped and left out.  The
+    prediction path is run once before the first timed prediction (its first call initialises the
+    library's inference state, ~0.5 s, as the solver's first launches are warmed before timing);
+    warm steps are counted in whole checks, so a warm run that reaches the error within the first
+    check_every updates counts check_every."""
     import torch
     S = _S()
     if prec is None:
         prec = S.SMRT_PREC_F32
+    if net is not None and len(res):
+        predict_fields(net, [res[0]], n, train_n)
+        torch.cuda.synchronize()
     out = []
     for re in res:
         row = {"re": re, "n": n, "prec": {0: "f64", 1: "f32"}.get(prec, prec)}
