@@ -587,8 +587,8 @@ constexpr int kRTX = 32, kRTY = 8, kRHX = kRTX + 2, kRHY = kRTY + 2;
 // it; f(t+1) of a node on the previous row then comes from registers: the populations arriving along
 // x from the neighbouring lanes by warp shuffles, those arriving along y from the rows kept before
 // and after it, and bounce-back terms from the node's own f*.  Collisions per node: 32/30 x
-// (kRSR + 2)/kRSR; no shared memory, no block barrier.  Sums: |u1-u0|^2, |u1|^2, rho0, rho0 ux0,
-// rho0 uy0.
+// (kRSR + 2)/kRSR; no shared memory, no block barrier; f(t) of the next row is loaded while the
+// current row collides.  Sums: |u1-u0|^2, |u1|^2, rho0, rho0 ux0, rho0 uy0.
 // Double offsets: u0 and u1 by moments_d and their difference.  Float offsets (the 32- and 16-bit
 // formats): the change is formed from the offset differences in float,
 //   u1 - u0 = (dj - u0 drho) / rho1,  drho = sum_a (g1_a - g0_a),  dj = sum_a c_a (g1_a - g0_a),
@@ -638,6 +638,7 @@ __device__ __forceinline__ bool sweep_pull(const typename Prec<PREC>::R *state, 
 #define SMRT_RESID_MIN_BLOCKS 3          // blocks per SM the register budget is set for (sweepable)
 #endif
 
+
 template <int PREC, int KIND, int MODE, bool SR = false>
 __global__ void __launch_bounds__(256, SMRT_RESID_MIN_BLOCKS)
 residual_kernel(const typename Prec<PREC>::R *__restrict__ state, const Params<typename Prec<PREC>::C> p,
@@ -663,13 +664,31 @@ residual_kernel(const typename Prec<PREC>::R *__restrict__ state, const Params<t
         C own2_2 = 0, in5_2 = 0, in6_2 = 0;
         #pragma unroll
         for (int a = 0; a < 9; ++a) own1[a] = g01[a] = 0;
+        // f(t) of the next row is pulled one iteration ahead, so its loads are in flight during the
+        // current row's collision
+        int wi_n = i, wj_n = r0 - 1;
+        C gn[9];
+        #pragma unroll
+        for (int a = 0; a < 9; ++a) gn[a] = 0;
+        bool has_n = sweep_pull<PREC, MODE>(state, p, wi_n, wj_n, gn);
         #pragma unroll 1
         for (int jj = -1; jj <= rows; ++jj) {
-            int wi = i, wj = r0 + jj;
             C g[9], pc[9];
+            const int wi = wi_n, wj = wj_n;
+            const bool has = has_n;
             #pragma unroll
-            for (int a = 0; a < 9; ++a) g[a] = pc[a] = 0;
-            if (sweep_pull<PREC, MODE>(state, p, wi, wj, g)) {
+            for (int a = 0; a < 9; ++a) {
+                g[a] = gn[a];
+                pc[a] = 0;
+            }
+            if (jj < rows) {
+                wi_n = i;
+                wj_n = r0 + jj + 1;
+                #pragma unroll
+                for (int a = 0; a < 9; ++a) gn[a] = 0;
+                has_n = sweep_pull<PREC, MODE>(state, p, wi_n, wj_n, gn);
+            }
+            if (has) {
                 #pragma unroll
                 for (int a = 0; a < 9; ++a) pc[a] = g[a];
                 collide<KIND, Prec<PREC>::kExactWeights>(p, pc);
