@@ -251,6 +251,107 @@ __device__ __forceinline__ void teardown(uint32_t tmem)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(COLS));
 }
 
+// Epilogue of accumulator columns c .. c + 31 of output-channel block n0 for one pixel (yy, xx) of
+// image img (one TMEM lane): plain y = alpha acc + beta y (on == 0), bias + SiLU (on == 1) or the
+// SiLU backward with the bias-gradient sums into sdb (on == 2; every lane of the warp takes part).
+template <int TN>
+__device__ __forceinline__ void epi_store32(const uint32_t r[32], int c, int n0, int cout, bool valid, int img,
+                                            int H, int W, int yy, int xx, size_t pix, float alpha, float beta,
+                                            float *yrow, int vec_y, const Epi &epi, float *sdb, int lane)
+{
+    const int col0 = n0 + c;
+    if (epi.on == 2) {
+        float v[32];
+        #pragma unroll
+        for (int j = 0; j < 32; j += 8) {
+            const bool ok = valid && col0 + j < cout;
+            #pragma unroll
+            for (int e = 0; e < 8; ++e) v[j + e] = ok ? __uint_as_float(r[j + e]) : 0.0f;
+            if (!ok) continue;
+            if (epi.act) {
+                const float4 *zq = reinterpret_cast<const float4 *>(epi.zin + pix * cout + col0 + j);
+                const float4 z0 = zq[0], z1 = zq[1];
+                const float zz[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
+                #pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const float sg = sigm(zz[e]);
+                    v[j + e] *= sg * (1.0f + zz[e] * (1.0f - sg));
+                }
+            }
+            if (epi.z) {
+                float4 *q = reinterpret_cast<float4 *>(epi.z + pix * cout + col0 + j);
+                q[0] = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                q[1] = make_float4(v[j + 4], v[j + 5], v[j + 6], v[j + 7]);
+            }
+            __half2 h[4];
+            #pragma unroll
+            for (int e = 0; e < 4; ++e) h[e] = __floats2half2_rn(v[j + 2 * e], v[j + 2 * e + 1]);
+            const size_t g = (size_t)(col0 + j) / 8, G = (size_t)cout / 8;
+            *reinterpret_cast<uint4 *>(epi.ab + (((size_t)img * G + g) * H * W + (size_t)yy * W + xx) * 8) =
+                *reinterpret_cast<uint4 *>(h);
+        }
+        if (epi.db) {
+            const float sum = warp_reduce_scatter32(v, lane);
+            atomicAdd(&sdb[c + lane], sum);
+        }
+        return;
+    }
+    if (!valid) return;
+    if (epi.on) {
+        #pragma unroll
+        for (int j = 0; j < 32; j += 8) {
+            if (col0 + j >= cout) break;
+            float v[8];
+            #pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = __uint_as_float(r[j + e]) + epi.bias[col0 + j + e];
+            if (epi.z) {
+                float4 *q = reinterpret_cast<float4 *>(epi.z + pix * cout + col0 + j);
+                q[0] = make_float4(v[0], v[1], v[2], v[3]);
+                q[1] = make_float4(v[4], v[5], v[6], v[7]);
+            }
+            if (epi.act) {
+                #pragma unroll
+                for (int e = 0; e < 8; ++e) v[e] = v[e] * sigm(v[e]);
+            }
+            if (epi.a) {
+                float4 *q = reinterpret_cast<float4 *>(epi.a + pix * cout + col0 + j);
+                q[0] = make_float4(v[0], v[1], v[2], v[3]);
+                q[1] = make_float4(v[4], v[5], v[6], v[7]);
+            }
+            if (epi.ab) {
+                __half2 h[4];
+                #pragma unroll
+                for (int e = 0; e < 4; ++e) h[e] = __floats2half2_rn(v[2 * e], v[2 * e + 1]);
+                const size_t g = (size_t)(col0 + j) / 8, G = (size_t)cout / 8;
+                *reinterpret_cast<uint4 *>(epi.ab + (((size_t)img * G + g) * H * W + (size_t)yy * W + xx) * 8) =
+                    *reinterpret_cast<uint4 *>(h);
+            }
+        }
+        return;
+    }
+    if (vec_y && col0 + 32 <= cout) {
+        #pragma unroll
+        for (int j = 0; j < 32; j += 4) {
+            float4 v = make_float4(alpha * __uint_as_float(r[j]), alpha * __uint_as_float(r[j + 1]),
+                                   alpha * __uint_as_float(r[j + 2]), alpha * __uint_as_float(r[j + 3]));
+            float4 *p = reinterpret_cast<float4 *>(yrow + col0 + j);
+            if (beta != 0.0f) {
+                const float4 o = *p;
+                v.x += beta * o.x; v.y += beta * o.y; v.z += beta * o.z; v.w += beta * o.w;
+            }
+            *p = v;
+        }
+    } else {
+        #pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            if (col0 + j >= cout) break;
+            float *p = yrow + col0 + j;
+            const float v = alpha * __uint_as_float(r[j]);
+            *p = (beta != 0.0f) ? v + beta * *p : v;
+        }
+    }
+}
+
 // ---- forward -------------------------------------------------------------------------------
 // grid (tiles in x, groups of MT tiles in y, N * output-channel blocks); wp points at this launch's
 // packed weights: block nb, chunk i is the 18 * TN * 8 halves at ((nb * nchunks + i) * 18 * TN * 8).
@@ -331,97 +432,7 @@ conv3_tma_kernel(const __grid_constant__ CUtensorMap tmx, const __half *__restri
         for (int c = 0; c < TN; c += 32) {
             uint32_t r[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mt * TN + c), r);
-            const int col0 = n0 + c;
-            if (epi.on == 2) {
-                float v[32];
-                #pragma unroll
-                for (int j = 0; j < 32; j += 8) {
-                    const bool ok = valid && col0 + j < cout;
-                    #pragma unroll
-                    for (int e = 0; e < 8; ++e) v[j + e] = ok ? __uint_as_float(r[j + e]) : 0.0f;
-                    if (!ok) continue;
-                    if (epi.act) {
-                        const float4 *zq = reinterpret_cast<const float4 *>(epi.zin + pix * cout + col0 + j);
-                        const float4 z0 = zq[0], z1 = zq[1];
-                        const float zz[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
-                        #pragma unroll
-                        for (int e = 0; e < 8; ++e) {
-                            const float sg = sigm(zz[e]);
-                            v[j + e] *= sg * (1.0f + zz[e] * (1.0f - sg));
-                        }
-                    }
-                    if (epi.z) {
-                        float4 *q = reinterpret_cast<float4 *>(epi.z + pix * cout + col0 + j);
-                        q[0] = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-                        q[1] = make_float4(v[j + 4], v[j + 5], v[j + 6], v[j + 7]);
-                    }
-                    __half2 h[4];
-                    #pragma unroll
-                    for (int e = 0; e < 4; ++e) h[e] = __floats2half2_rn(v[j + 2 * e], v[j + 2 * e + 1]);
-                    const size_t g = (size_t)(col0 + j) / 8, G = (size_t)cout / 8;
-                    *reinterpret_cast<uint4 *>(epi.ab + (((size_t)img * G + g) * H * W + (size_t)yy * W + xx) * 8) =
-                        *reinterpret_cast<uint4 *>(h);
-                }
-                if (epi.db) {
-                    const float sum = warp_reduce_scatter32(v, lane);
-                    atomicAdd(&sdb[c + lane], sum);
-                }
-                continue;
-            }
-            if (!valid) continue;
-            if (epi.on) {
-                #pragma unroll
-                for (int j = 0; j < 32; j += 8) {
-                    if (col0 + j >= cout) break;
-                    float v[8];
-                    #pragma unroll
-                    for (int e = 0; e < 8; ++e) v[e] = __uint_as_float(r[j + e]) + epi.bias[col0 + j + e];
-                    if (epi.z) {
-                        float4 *q = reinterpret_cast<float4 *>(epi.z + pix * cout + col0 + j);
-                        q[0] = make_float4(v[0], v[1], v[2], v[3]);
-                        q[1] = make_float4(v[4], v[5], v[6], v[7]);
-                    }
-                    if (epi.act) {
-                        #pragma unroll
-                        for (int e = 0; e < 8; ++e) v[e] = v[e] * sigm(v[e]);
-                    }
-                    if (epi.a) {
-                        float4 *q = reinterpret_cast<float4 *>(epi.a + pix * cout + col0 + j);
-                        q[0] = make_float4(v[0], v[1], v[2], v[3]);
-                        q[1] = make_float4(v[4], v[5], v[6], v[7]);
-                    }
-                    if (epi.ab) {
-                        __half2 h[4];
-                        #pragma unroll
-                        for (int e = 0; e < 4; ++e) h[e] = __floats2half2_rn(v[2 * e], v[2 * e + 1]);
-                        const size_t g = (size_t)(col0 + j) / 8, G = (size_t)cout / 8;
-                        *reinterpret_cast<uint4 *>(epi.ab + (((size_t)img * G + g) * H * W + (size_t)yy * W + xx) * 8) =
-                            *reinterpret_cast<uint4 *>(h);
-                    }
-                }
-                continue;
-            }
-            if (vec_y && col0 + 32 <= cout) {
-                #pragma unroll
-                for (int j = 0; j < 32; j += 4) {
-                    float4 v = make_float4(alpha * __uint_as_float(r[j]), alpha * __uint_as_float(r[j + 1]),
-                                           alpha * __uint_as_float(r[j + 2]), alpha * __uint_as_float(r[j + 3]));
-                    float4 *p = reinterpret_cast<float4 *>(yrow + col0 + j);
-                    if (beta != 0.0f) {
-                        const float4 o = *p;
-                        v.x += beta * o.x; v.y += beta * o.y; v.z += beta * o.z; v.w += beta * o.w;
-                    }
-                    *p = v;
-                }
-            } else {
-                #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    if (col0 + j >= cout) break;
-                    float *p = yrow + col0 + j;
-                    const float v = alpha * __uint_as_float(r[j]);
-                    *p = (beta != 0.0f) ? v + beta * *p : v;
-                }
-            }
+            epi_store32<TN>(r, c, n0, cout, valid, img, H, W, yy, xx, pix, alpha, beta, yrow, vec_y, epi, sdb, lane);
         }
     }
     if (epi.on == 2 && epi.db && !failed) {

@@ -107,6 +107,7 @@ def _conv(n, h, w, C, cout, alpha, beta, seed):
     (10, 70, 40, 32, 136),    # stacked tile pairs (300 CTAs), the last pair partly outside, two N tiles
     (16, 48, 56, 80, 256),    # stacked pairs over 5 chunks (the stages are reused)
     (16, 70, 44, 48, 48),     # a grid where pairs would apply, but 64-wide tiles run single
+    (16, 160, 96, 32, 24),    # 1,920 tiles of one 32-wide output block, 2 chunks
 ])
 def test_conv3_tma_matches_fp64_product_of_the_same_halves(n, h, w, C, cout):
     got, exp, err, _ = _conv(n, h, w, C, cout, 0.75, 0.5, seed=C * 1000 + cout)
@@ -137,11 +138,12 @@ def test_conv3_tma_agrees_with_the_gather_kernel():
 
 
 @pytest.mark.parametrize("act", [1, 0])
-def test_conv3_tma_bias_act_equals_the_unfused_pair_bitwise(act):
+@pytest.mark.parametrize("n,h,w,C,cout", [(2, 21, 13, 32, 136), (2, 37, 21, 32, 24), (3, 40, 18, 48, 64)])
+def test_conv3_tma_bias_act_equals_the_unfused_pair_bitwise(act, n, h, w, C, cout):
     """Bias and SiLU in the convolution's epilogue give exactly what smrt_nn_conv3_tma followed by
-    smrt_nn_bias_act_blocked gives (z, a and the blocked halves), on ragged tiles and two N tiles."""
+    smrt_nn_bias_act_blocked gives (z, a and the blocked halves), on ragged tiles: two N tiles of
+    128, and one output-channel block of 32 or 64."""
     import torch
-    n, h, w, C, cout = 2, 21, 13, 32, 136
     r = _rng(90 + act)
     x = r.normal(size=(n, h, w, C)).astype(np.float16)
     wt = torch.tensor(r.normal(size=(cout, 9 * C)).astype(np.float16), device="cuda")
