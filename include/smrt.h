@@ -221,26 +221,6 @@ SMRT_API int smrt_set_f(smrt_t *h, const double *f);
  * flag clears. */
 SMRT_API int smrt_init_macros(smrt_t *h, const double *rho, const double *u);
 
-/* One job from host fields to host fields: the effect of
- *   smrt_init_macros(h, rho_in, u_in); smrt_step(h, n); smrt_macros(h, rho_out, u_out);
- * (Eqs. feq-full, SmrtLBM-1 n times, fea-0), with the same results bit for bit.
- * rho_in / u_in: double[ny][nx] / double[2][ny][nx], both or neither (neither:
- * start from the current state); rho_out / u_out: either may be NULL.  Arrays
- * are host or device memory, as in smrt_init_macros and smrt_macros.
- * When some array is page-locked host memory, every array is page-locked or on
- * the device, the layout is SMRT_LAYOUT_AB, 1 <= n <= 64 and ny >= 512, the
- * call overlaps the host link with the updates: the lattice is cut into row
- * chunks (256 rows or more, at most 32); the initial state of each chunk is read
- * over the link on one stream, the updates of each chunk run on the handle's
- * stream as soon as the chunks they depend on are ready (update k of a chunk
- * needs update k - 1 of it and of its two neighbours), and the macros of each
- * finished chunk go back over the link on a third stream while later chunks
- * still update.  Otherwise it makes the three calls in order.  The call returns
- * when the outputs are written; t advances by n; the divergence flag is checked
- * as in smrt_step. */
-SMRT_API int smrt_run(smrt_t *h, const double *rho_in, const double *u_in, long long n, double *rho_out,
-                      double *u_out);
-
 /* Number of updates applied so far (t); -1 for a NULL handle. */
 SMRT_API long long smrt_time(const smrt_t *h);
 

@@ -177,17 +177,6 @@ def smrt_init_macros(h: Handle, rho, u) -> None:
                                         _ptr(u, (2, h.ny, h.nx), "u", False)), h)
 
 
-def smrt_run(h: Handle, rho_in=None, u_in=None, n: int = 0, rho_out=None, u_out=None) -> None:
-    """smrt_init_macros(rho_in, u_in) (if given), n updates, smrt_macros(rho_out, u_out), in one call
-    that overlaps the host-link transfers of page-locked arrays with the updates."""
-    if n < 0:
-        raise ValueError("n must be >= 0")
-    _check(_lib.load().smrt_run(h, _ptr(rho_in, (h.ny, h.nx), "rho_in", False),
-                                _ptr(u_in, (2, h.ny, h.nx), "u_in", False), int(n),
-                                _ptr(rho_out, (h.ny, h.nx), "rho_out", True),
-                                _ptr(u_out, (2, h.ny, h.nx), "u_out", True)), h)
-
-
 def smrt_time(h: Handle) -> int:
     return int(_lib.load().smrt_time(h))
 

@@ -32,7 +32,6 @@ SIGNATURES = [
     ("smrt_get_f", c_int, [c_void_p, c_void_p]),
     ("smrt_set_f", c_int, [c_void_p, c_void_p]),
     ("smrt_init_macros", c_int, [c_void_p, c_void_p, c_void_p]),
-    ("smrt_run", c_int, [c_void_p, c_void_p, c_void_p, c_longlong, c_void_p, c_void_p]),
     ("smrt_time", c_longlong, [c_void_p]),
     ("smrt_set_time", c_int, [c_void_p, c_longlong]),
     ("smrt_device_bytes", c_size_t, [c_void_p]),

@@ -9,7 +9,6 @@
 
 #include <new>
 #include <string>
-#include <vector>
 
 #include "internal.h"
 #include "smrt.h"
@@ -67,10 +66,6 @@ struct smrt_t {
     size_t dev_bytes = 0;
     long long t = 0;
     std::string err = "no error";
-    // smrt_run's pipeline: streams for the host-link reads and writes, one event per row chunk each
-    cudaStream_t s_in = nullptr, s_out = nullptr;
-    std::vector<cudaEvent_t> ev_in, ev_out;
-    cudaEvent_t ev_start = nullptr, ev_join = nullptr;
 };
 
 namespace {
@@ -189,16 +184,6 @@ void release(smrt_t *h)
     h->h_flag = nullptr;
     h->stage_bytes = 0;
     h->dev_bytes = 0;
-    for (cudaEvent_t e : h->ev_in) cudaEventDestroy(e);
-    for (cudaEvent_t e : h->ev_out) cudaEventDestroy(e);
-    h->ev_in.clear();
-    h->ev_out.clear();
-    if (h->ev_start) cudaEventDestroy(h->ev_start);
-    if (h->ev_join) cudaEventDestroy(h->ev_join);
-    if (h->s_in) cudaStreamDestroy(h->s_in);
-    if (h->s_out) cudaStreamDestroy(h->s_out);
-    h->ev_start = h->ev_join = nullptr;
-    h->s_in = h->s_out = nullptr;
     h->ready = false;
 }
 
@@ -319,45 +304,6 @@ int begin(smrt_t *h)
 {
     if (!h) return SMRT_ERR_ARG;
     return materialize(h);
-}
-
-// The pipeline of smrt_run: row chunks of at least kRunMinRows rows, at most kRunMaxChunks of them,
-// for runs of at most kRunMaxSteps updates (longer runs spend their time in the updates).
-constexpr int kRunMinRows = 256, kRunMaxChunks = 32;
-constexpr long long kRunMaxSteps = 64;
-
-int run_resources(smrt_t *h, int chunks)
-{
-    cudaError_t e = cudaSuccess;
-    if (!h->s_in) {
-        int lo = 0, hi = 0;
-        e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
-        // the link-bound chunk kernels get the higher priority: they hold few blocks, and the link
-        // should never wait for blocks of an update
-        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->s_in, cudaStreamNonBlocking, hi);
-        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->s_out, cudaStreamNonBlocking, hi);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
-    }
-    while (e == cudaSuccess && (int)h->ev_in.size() < chunks) {
-        cudaEvent_t a = nullptr, b = nullptr;
-        e = cudaEventCreateWithFlags(&a, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b, cudaEventDisableTiming);
-        if (e == cudaSuccess) {
-            h->ev_in.push_back(a);
-            h->ev_out.push_back(b);
-        }
-    }
-    return e == cudaSuccess ? SMRT_OK : cuda_fail(h, e, "smrt_run: streams and events");
-}
-
-// Blocks of a chunk kernel that reads or writes host memory: two per SM reach the host link's rate
-// (one per SM already reaches 97 % of it) and leave the SMs to the updates.
-int link_blocks(const smrt_t *h)
-{
-    int sms = 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || sms < 1) sms = 148;
-    return 2 * sms;
 }
 
 } // namespace
@@ -666,117 +612,6 @@ int smrt_init_macros(smrt_t *h, const double *rho, const double *u)
                                       ku == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
         CUDA_TRY(h, T.init_macros(current_mode(h), state, srho, su, r0, rows, p, h->stream));
     }
-    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-    return SMRT_OK;
-}
-
-int smrt_run(smrt_t *h, const double *rho_in, const double *u_in, long long n, double *rho_out, double *u_out)
-{
-    smrt::TraceRange trace("smrt_run");
-    if (!h) return SMRT_ERR_ARG;
-    if (n < 0) return fail(h, SMRT_ERR_ARG, "smrt_run: n must be >= 0 (got %lld)", n);
-    if ((rho_in == nullptr) != (u_in == nullptr))
-        return fail(h, SMRT_ERR_ARG, "smrt_run: rho_in and u_in are given together or not at all");
-    int rc = begin(h);
-    if (rc != SMRT_OK) return rc;
-    DeviceGuard g(h->device);
-    CUDA_TRY(h, g.err);
-    const void *dri = rho_in, *dui = u_in, *dro = rho_out, *duo = u_out;
-    const int kri = rho_in ? classify(h, rho_in, &dri) : 1, kui = u_in ? classify(h, u_in, &dui) : 1;
-    const int kro = rho_out ? classify(h, rho_out, &dro) : 1, kuo = u_out ? classify(h, u_out, &duo) : 1;
-    if (kri == -1 || kui == -1 || kro == -1 || kuo == -1)
-        return fail(h, SMRT_ERR_ARG, "smrt_run: pointer on another device");
-    const bool direct = kri > 0 && kui > 0 && kro > 0 && kuo > 0;
-    const bool host = kri == 2 || kui == 2 || kro == 2 || kuo == 2;
-    const int chunks = h->ny / kRunMinRows < kRunMaxChunks ? h->ny / kRunMinRows : kRunMaxChunks;
-    if (!(direct && host && h->layout == SMRT_LAYOUT_AB && n >= 1 && n <= kRunMaxSteps && chunks >= 2)) {
-        // nothing to overlap: the three calls in order
-        if (rho_in && (rc = smrt_init_macros(h, rho_in, u_in)) != SMRT_OK) return rc;
-        if ((rc = smrt_step(h, n)) != SMRT_OK) return rc;
-        return (rho_out || u_out) ? smrt_macros(h, rho_out, u_out) : SMRT_OK;
-    }
-    if ((rc = run_resources(h, chunks)) != SMRT_OK) return rc;
-    const KernelTable &T = table_for(h->prec);
-    HostParams p = host_params(h);
-    const int rows_per = (h->ny + chunks - 1) / chunks, nb = link_blocks(h);
-    const size_t plane = (size_t)h->nx * h->ny;
-    auto r0_of = [&](int c) { return c * rows_per; };
-    auto r1_of = [&](int c) { return (c + 1) * rows_per < h->ny ? (c + 1) * rows_per : h->ny; };
-    const long long t0 = h->t;
-    const int cur0 = h->cur;
-
-    // the chunk streams start after everything already queued on the handle's stream
-    if (rho_in) CUDA_TRY(h, cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream));
-    CUDA_TRY(h, cudaEventRecord(h->ev_start, h->stream));
-    CUDA_TRY(h, cudaStreamWaitEvent(h->s_in, h->ev_start, 0));
-    CUDA_TRY(h, cudaStreamWaitEvent(h->s_out, h->ev_start, 0));
-    if (rho_in) {
-        // the initial state, chunk by chunk over the host link
-        for (int c = 0; c < chunks; ++c) {
-            const int r0 = r0_of(c);
-            CUDA_TRY(h, T.init_macros_rows(MODE_AB, h->buf[cur0], (const double *)dri + (size_t)r0 * h->nx,
-                                           (const double *)dui + (size_t)r0 * h->nx, plane, r0, r1_of(c) - r0, p,
-                                           kri == 2 || kui == 2 ? nb : 0, h->s_in));
-            CUDA_TRY(h, cudaEventRecord(h->ev_in[c], h->s_in));
-        }
-    }
-    // Update k of chunk c reads state k - 1 of chunks c - 1, c, c + 1 (its halo rows; the first and
-    // last chunk are neighbours when y is periodic) and overwrites state k - 2, which those chunks'
-    // update k - 1 reads: it follows updates k - 1 of all three.  Update 1 reads only what the
-    // initial state of its own chunk wrote (each node's f^eq goes where that node pulls it from).
-    // Chunk c is final once update n of its three chunks is done.  The handle's stream gets, greedily,
-    // every update whose predecessors are already queued, then waits for the next chunk's initial
-    // state; the output stream takes each final chunk's macros while later updates continue.
-    const bool wrap = ((h->bc >> 4) & 3u) == SMRT_BC_PERIODIC;
-    std::vector<long long> done(chunks, 0);
-    std::vector<char> sent(chunks, 0);
-    auto nbr = [&](int c, int d) { const int m = c + d; return wrap ? (m + chunks) % chunks : m; };
-    auto level = [&](int c) { return (c < 0 || c >= chunks) ? (long long)n : done[c]; };   // no neighbour
-    const bool out = rho_out || u_out;
-    int loaded = rho_in ? 0 : chunks;
-    int remaining = chunks * (int)n, outs = out ? chunks : 0;
-    while (remaining > 0 || outs > 0) {
-        bool progress = true;
-        while (progress) {
-            progress = false;
-            for (int c = 0; c < chunks; ++c) {
-                const long long k = done[c] + 1;
-                if (k > n) continue;
-                const bool ready = (k == 1) ? c < loaded
-                                            : level(nbr(c, -1)) >= k - 1 && level(nbr(c, 1)) >= k - 1;
-                if (!ready) continue;
-                p.t = t0 + k - 1;
-                cudaError_t e = T.step_rows(h->collision, h->buf[(cur0 + k - 1) & 1], h->buf[(cur0 + k) & 1], p,
-                                            r0_of(c), r1_of(c), h->stream);
-                if (e != cudaSuccess) return cuda_fail(h, e, "smrt_run: update launch");
-                done[c] = k;
-                --remaining;
-                progress = true;
-            }
-            for (int c = 0; out && c < chunks; ++c) {
-                if (sent[c] || done[c] < n || level(nbr(c, -1)) < n || level(nbr(c, 1)) < n) continue;
-                sent[c] = 1;
-                --outs;
-                const int r0 = r0_of(c);
-                CUDA_TRY(h, cudaEventRecord(h->ev_out[c], h->stream));
-                CUDA_TRY(h, cudaStreamWaitEvent(h->s_out, h->ev_out[c], 0));
-                CUDA_TRY(h, T.macros_rows(MODE_AB, h->buf[(cur0 + n) & 1],
-                                          rho_out ? (double *)dro + (size_t)r0 * h->nx : nullptr,
-                                          u_out ? (double *)duo + (size_t)r0 * h->nx : nullptr, plane, r0,
-                                          r1_of(c) - r0, p, kro == 2 || kuo == 2 ? nb : 0, h->s_out));
-            }
-        }
-        if (remaining == 0 && outs == 0) break;
-        if (loaded >= chunks) return fail(h, SMRT_ERR_STATE, "smrt_run: pipeline stalled (internal error)");
-        CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_in[loaded], 0));
-        ++loaded;
-    }
-    h->t = t0 + n;
-    h->cur = (int)((cur0 + n) & 1);
-    // later work on the handle's stream follows the output stream
-    CUDA_TRY(h, cudaEventRecord(h->ev_join, h->s_out));
-    CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
-    if (h->check_div) return smrt_sync(h);
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return SMRT_OK;
 }

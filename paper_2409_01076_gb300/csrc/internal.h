@@ -61,15 +61,6 @@ struct KernelTable {
                           int rows, const HostParams &p, cudaStream_t s);
     cudaError_t (*residual)(int kind, int mode, const void *state, const HostParams &p,
                             const Scratch &scratch, cudaStream_t s);
-    // rows [r0, r1) only, two-buffer layout (the pipelined smrt_run)
-    cudaError_t (*step_rows)(int kind, const void *src, void *dst, const HostParams &p, int r0, int r1,
-                             cudaStream_t s);
-    // rows [row0, row0 + rows) of whole-field arrays: rho, u point at row row0, u_y at uy_off from u_x;
-    // at most max_blocks blocks (0: one thread per node)
-    cudaError_t (*init_macros_rows)(int mode, void *state, const double *rho, const double *u, size_t uy_off,
-                                    int row0, int rows, const HostParams &p, int max_blocks, cudaStream_t s);
-    cudaError_t (*macros_rows)(int mode, const void *state, double *rho, double *u, size_t uy_off, int row0,
-                               int rows, const HostParams &p, int max_blocks, cudaStream_t s);
     size_t elem_bytes;
 };
 

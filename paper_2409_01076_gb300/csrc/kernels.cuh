@@ -35,9 +35,6 @@ struct StepGeom {
     // (a power of two <= 32) owning seg * VEC consecutive columns; a row holds `spr` segments,
     // the interior `tasks` = (ny - 2) * spr of them, and a block of BX threads takes BX / seg.
     int seg_log2, spr, tasks;
-    // row window (step_geom_rows): interior rows start at j0; the band holds nbot nodes of row 0
-    // and ntop nodes of row ny - 1 (nx or 0 each), then the edge columns of the window's interior rows
-    int j0, nbot, ntop;
 };
 
 // edge_in (the two-buffer layout only): the first and, when nx % VEC == 0, the last VEC-wide
@@ -68,27 +65,6 @@ inline StepGeom step_geom(int nx, int ny, bool edge_in)
     g.seg_log2 = 5;
     g.spr = 0;
     g.tasks = 0;
-    g.j0 = 1;
-    g.nbot = nx;
-    g.ntop = ny >= 2 ? nx : 0;
-    return g;
-}
-
-// The nodes of rows [r0, r1) only (0 <= r0 < r1 <= ny): the same interior and band structure
-// restricted to the window, so that a step of the whole lattice is the union of the steps of
-// disjoint windows, node for node.
-template <int VEC, int BX>
-inline StepGeom step_geom_rows(int nx, int ny, bool edge_in, int r0, int r1)
-{
-    StepGeom g = step_geom<VEC, BX>(nx, ny, edge_in);
-    const int lo = r0 > 1 ? r0 : 1, hi = r1 < ny - 1 ? r1 : ny - 1;
-    const int rows = hi > lo ? hi - lo : 0;
-    g.j0 = lo;
-    g.n_int_blocks = g.bpr * rows;
-    g.nbot = r0 == 0 ? nx : 0;
-    g.ntop = (ny >= 2 && r1 == ny) ? nx : 0;
-    const long long bw = (long long)g.L + (long long)(nx - g.R);
-    g.n_edge = (long long)g.nbot + g.ntop + (long long)rows * bw;
     return g;
 }
 
@@ -301,14 +277,14 @@ __device__ __forceinline__ void step_block(const typename Prec<PREC>::R *src, ty
         long long e = (long long)(b - geo.n_int_blocks) * BX + tid;
         if (e >= geo.n_edge) return;
         int i, j;
-        if (e < geo.nbot) {
+        if (e < p.nx) {
             i = (int)e; j = 0;
-        } else if (e < (long long)geo.nbot + geo.ntop) {
-            i = (int)(e - geo.nbot); j = p.ny - 1;
+        } else if (e < 2LL * p.nx && p.ny >= 2) {
+            i = (int)(e - p.nx); j = p.ny - 1;
         } else {
-            long long m = e - geo.nbot - geo.ntop;
+            long long m = e - 2LL * p.nx;
             int bw = geo.L + (p.nx - geo.R);
-            j = geo.j0 + (int)(m / bw);
+            j = 1 + (int)(m / bw);
             int k = (int)(m % bw);
             i = k < geo.L ? k : geo.R + (k - geo.L);
         }
@@ -325,10 +301,10 @@ __device__ __forceinline__ void step_block(const typename Prec<PREC>::R *src, ty
         const int task = b * (BX >> geo.seg_log2) + (tid >> geo.seg_log2);
         valid = task < geo.tasks;
         const int tk = valid ? task : 0;
-        j = geo.j0 + tk / geo.spr;
+        j = 1 + tk / geo.spr;
         i0 = ((tk % geo.spr) << geo.seg_log2) * VEC + (tid & (seg - 1)) * VEC;
     } else {
-        j = geo.j0 + b / geo.bpr;
+        j = 1 + b / geo.bpr;
         i0 = (b % geo.bpr) * (BX * VEC) + tid * VEC;
     }
     const bool active = valid && (i0 >= geo.L) && (i0 + VEC <= geo.R);
@@ -471,47 +447,44 @@ __device__ __forceinline__ void init_store_f(typename Prec<PREC>::R *state, cons
 // f = f^eq(rho, u) (Eq. feq-full), written as offsets through the pull map;
 // rho == NULL selects rho = 1, u = 0.  rho and u may be device memory or host memory
 // the device can address (page-locked and mapped).
-// rho[q], u[q] (u_x) and u[uy_off + q] (u_y) hold node q = r * nx + i of row row0 + r; a thread
-// takes every (gridDim.x * blockDim.x)-th node.
 template <int PREC, int MODE>
 __global__ void init_macros_kernel(typename Prec<PREC>::R *state, const double *rho, const double *u,
-                                   size_t uy_off, int row0, int rows, const Params<typename Prec<PREC>::C> p)
+                                   int row0, int rows, const Params<typename Prec<PREC>::C> p)
 {
     using P = Prec<PREC>;
-    const long long n = (long long)rows * p.nx;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-         t += (long long)gridDim.x * blockDim.x) {
-        int r = (int)(t / p.nx), i = (int)(t % p.nx), j = row0 + r;
-        size_t q = (size_t)r * p.nx + i;
-        double d = 1.0, ux = 0.0, uy = 0.0;           // rho == NULL: the resting state
-        if (rho) {
-            d = rho[q];
-            ux = u[q];
-            uy = u[uy_off + q];
+    long long n = (long long)rows * p.nx;
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int r = (int)(t / p.nx), i = (int)(t % p.nx), j = row0 + r;
+    size_t q = (size_t)r * p.nx + i;
+    double d = 1.0, ux = 0.0, uy = 0.0;           // rho == NULL: the resting state
+    if (rho) {
+        d = rho[q];
+        ux = u[q];
+        uy = u[(size_t)rows * p.nx + q];
+    }
+    if constexpr (PREC == SMRT_PREC_F64) {
+        double uu = ux * ux + uy * uy;
+        #pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            double eu = ex(a) * ux + ey(a) * uy;
+            double g = wgt<double>(a) * ((d - 1.0) + d * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu));
+            Loc L = pull_loc<MODE>(p, a, i, j);
+            if (L.side >= 0) g -= (double)p.corr[L.side][a];
+            state[at(p.plane, p.pitch, L.plane, L.j, L.i)] = P::to_r((typename P::C)g);
         }
-        if constexpr (PREC == SMRT_PREC_F64) {
-            double uu = ux * ux + uy * uy;
-            #pragma unroll
-            for (int a = 0; a < 9; ++a) {
-                double eu = ex(a) * ux + ey(a) * uy;
-                double g = wgt<double>(a) * ((d - 1.0) + d * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu));
-                Loc L = pull_loc<MODE>(p, a, i, j);
-                if (L.side >= 0) g -= (double)p.corr[L.side][a];
-                state[at(p.plane, p.pitch, L.plane, L.j, L.i)] = P::to_r((typename P::C)g);
-            }
-        } else {
-            const float drho = (float)(d - 1.0), df = (float)d, fx = (float)ux, fy = (float)uy;
-            const float uu = fx * fx + fy * fy;
-            init_store_f<PREC, MODE, 0>(state, p, i, j, drho, df, fx, fy, uu);
-            init_store_f<PREC, MODE, 1>(state, p, i, j, drho, df, fx, fy, uu);
-            init_store_f<PREC, MODE, 2>(state, p, i, j, drho, df, fx, fy, uu);
-            init_store_f<PREC, MODE, 3>(state, p, i, j, drho, df, fx, fy, uu);
-            init_store_f<PREC, MODE, 4>(state, p, i, j, drho, df, fx, fy, uu);
-            init_store_f<PREC, MODE, 5>(state, p, i, j, drho, df, fx, fy, uu);
-            init_store_f<PREC, MODE, 6>(state, p, i, j, drho, df, fx, fy, uu);
-            init_store_f<PREC, MODE, 7>(state, p, i, j, drho, df, fx, fy, uu);
-            init_store_f<PREC, MODE, 8>(state, p, i, j, drho, df, fx, fy, uu);
-        }
+    } else {
+        const float drho = (float)(d - 1.0), df = (float)d, fx = (float)ux, fy = (float)uy;
+        const float uu = fx * fx + fy * fy;
+        init_store_f<PREC, MODE, 0>(state, p, i, j, drho, df, fx, fy, uu);
+        init_store_f<PREC, MODE, 1>(state, p, i, j, drho, df, fx, fy, uu);
+        init_store_f<PREC, MODE, 2>(state, p, i, j, drho, df, fx, fy, uu);
+        init_store_f<PREC, MODE, 3>(state, p, i, j, drho, df, fx, fy, uu);
+        init_store_f<PREC, MODE, 4>(state, p, i, j, drho, df, fx, fy, uu);
+        init_store_f<PREC, MODE, 5>(state, p, i, j, drho, df, fx, fy, uu);
+        init_store_f<PREC, MODE, 6>(state, p, i, j, drho, df, fx, fy, uu);
+        init_store_f<PREC, MODE, 7>(state, p, i, j, drho, df, fx, fy, uu);
+        init_store_f<PREC, MODE, 8>(state, p, i, j, drho, df, fx, fy, uu);
     }
 }
 
@@ -583,25 +556,23 @@ __device__ __forceinline__ void moments_any(const float g[9], double &rho, doubl
     moments_f(g, rho, ux, uy);
 }
 
-// Outputs laid out as the inputs of init_macros_kernel (u_y at uy_off from u_x).
 template <int PREC, int MODE>
-__global__ void macros_kernel(const typename Prec<PREC>::R *state, double *rho, double *u, size_t uy_off,
-                              int row0, int rows, const Params<typename Prec<PREC>::C> p)
+__global__ void macros_kernel(const typename Prec<PREC>::R *state, double *rho, double *u, int row0,
+                              int rows, const Params<typename Prec<PREC>::C> p)
 {
-    const long long n = (long long)rows * p.nx;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-         t += (long long)gridDim.x * blockDim.x) {
-        int r = (int)(t / p.nx), i = (int)(t % p.nx);
-        typename Prec<PREC>::C g[9];
-        pull_canonical<PREC, MODE>(state, p, i, row0 + r, g);
-        double rr, ux, uy;
-        moments_any(g, rr, ux, uy);
-        size_t q = (size_t)r * p.nx + i;
-        if (rho) rho[q] = rr;
-        if (u) {
-            u[q] = ux;
-            u[uy_off + q] = uy;
-        }
+    long long n = (long long)rows * p.nx;
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int r = (int)(t / p.nx), i = (int)(t % p.nx);
+    typename Prec<PREC>::C g[9];
+    pull_canonical<PREC, MODE>(state, p, i, row0 + r, g);
+    double rr, ux, uy;
+    moments_any(g, rr, ux, uy);
+    size_t q = (size_t)r * p.nx + i;
+    if (rho) rho[q] = rr;
+    if (u) {
+        u[q] = ux;
+        u[(size_t)rows * p.nx + q] = uy;
     }
 }
 
@@ -891,42 +862,6 @@ cudaError_t launch_step_km(const void *src, void *dst, const HostParams &hp, cud
     return cudaGetLastError();
 }
 
-// One step of the nodes of rows [r0, r1) only (two-buffer layout).
-template <int PREC, int KIND>
-cudaError_t launch_step_rows_k(const void *src, void *dst, const HostParams &hp, int r0, int r1, cudaStream_t s)
-{
-    using P = Prec<PREC>;
-    using R = typename P::R;
-    constexpr int VEC = Tune<PREC>::VEC, BX = Tune<PREC>::BX;
-    const Params<typename P::C> p = make_params<typename P::C>(hp);
-    const StepGeom geo = step_geom_rows<VEC, BX>(hp.nx, hp.ny, true, r0, r1);
-    const long long blocks = (long long)geo.n_int_blocks + (geo.n_edge + BX - 1) / BX;
-    if (blocks <= 0) return cudaSuccess;
-    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    if constexpr (PREC == SMRT_PREC_F16 || PREC == SMRT_PREC_BF16) {
-        if (hp.rounding == SMRT_ROUND_STOCHASTIC) {
-            step_kernel<PREC, KIND, MODE_AB, VEC, BX, true><<<(unsigned)blocks, BX, 0, s>>>(
-                (const R *)src, (R *)dst, p, geo);
-            return cudaGetLastError();
-        }
-    }
-    step_kernel<PREC, KIND, MODE_AB, VEC, BX><<<(unsigned)blocks, BX, 0, s>>>((const R *)src, (R *)dst, p, geo);
-    return cudaGetLastError();
-}
-
-template <int PREC>
-cudaError_t launch_step_rows(int kind, const void *src, void *dst, const HostParams &hp, int r0, int r1,
-                             cudaStream_t s)
-{
-    if (r0 < 0 || r1 > hp.ny || r0 >= r1) return cudaErrorInvalidValue;
-    switch (kind) {
-    case SMRT_COLLISION_SMRT: return launch_step_rows_k<PREC, SMRT_COLLISION_SMRT>(src, dst, hp, r0, r1, s);
-    case SMRT_COLLISION_SRT: return launch_step_rows_k<PREC, SMRT_COLLISION_SRT>(src, dst, hp, r0, r1, s);
-    case SMRT_COLLISION_TWO_TAU: return launch_step_rows_k<PREC, SMRT_COLLISION_TWO_TAU>(src, dst, hp, r0, r1, s);
-    default: return cudaErrorInvalidValue;
-    }
-}
-
 template <int PREC, int KIND>
 cudaError_t launch_step_k(int mode, const void *src, void *dst, const HostParams &hp, cudaStream_t s)
 {
@@ -995,24 +930,7 @@ cudaError_t launch_init_macros(int mode, void *state, const double *rho, const d
     const Params<typename P::C> p = make_params<typename P::C>(hp);
     if (rows <= 0) return cudaSuccess;
     const unsigned nb = node_blocks(rows, hp.nx, 256);
-    SMRT_MODE_SWITCH(mode, (init_macros_kernel<PREC, M><<<nb, 256, 0, s>>>((typename P::R *)state, rho, u,
-                                                                         (size_t)rows * hp.nx, row0, rows, p)));
-    return cudaGetLastError();
-}
-
-// init_macros for rows [row0, row0 + rows) of whole-field arrays (u_y at uy_off from u_x; rho and u
-// point at row row0), on at most max_blocks blocks of 256 threads.
-template <int PREC>
-cudaError_t launch_init_macros_rows(int mode, void *state, const double *rho, const double *u, size_t uy_off,
-                                    int row0, int rows, const HostParams &hp, int max_blocks, cudaStream_t s)
-{
-    using P = Prec<PREC>;
-    const Params<typename P::C> p = make_params<typename P::C>(hp);
-    if (rows <= 0) return cudaSuccess;
-    unsigned nb = node_blocks(rows, hp.nx, 256);
-    if (max_blocks > 0 && nb > (unsigned)max_blocks) nb = (unsigned)max_blocks;
-    SMRT_MODE_SWITCH(mode, (init_macros_kernel<PREC, M><<<nb, 256, 0, s>>>((typename P::R *)state, rho, u, uy_off,
-                                                                         row0, rows, p)));
+    SMRT_MODE_SWITCH(mode, (init_macros_kernel<PREC, M><<<nb, 256, 0, s>>>((typename P::R *)state, rho, u, row0, rows, p)));
     return cudaGetLastError();
 }
 
@@ -1024,23 +942,7 @@ cudaError_t launch_macros(int mode, const void *state, double *rho, double *u, i
     const Params<typename P::C> p = make_params<typename P::C>(hp);
     if (rows <= 0) return cudaSuccess;
     const unsigned nb = node_blocks(rows, hp.nx, 256);
-    SMRT_MODE_SWITCH(mode, (macros_kernel<PREC, M><<<nb, 256, 0, s>>>((const typename P::R *)state, rho, u,
-                                                                    (size_t)rows * hp.nx, row0, rows, p)));
-    return cudaGetLastError();
-}
-
-// macros of rows [row0, row0 + rows) into whole-field arrays (as launch_init_macros_rows).
-template <int PREC>
-cudaError_t launch_macros_rows(int mode, const void *state, double *rho, double *u, size_t uy_off, int row0,
-                               int rows, const HostParams &hp, int max_blocks, cudaStream_t s)
-{
-    using P = Prec<PREC>;
-    const Params<typename P::C> p = make_params<typename P::C>(hp);
-    if (rows <= 0) return cudaSuccess;
-    unsigned nb = node_blocks(rows, hp.nx, 256);
-    if (max_blocks > 0 && nb > (unsigned)max_blocks) nb = (unsigned)max_blocks;
-    SMRT_MODE_SWITCH(mode, (macros_kernel<PREC, M><<<nb, 256, 0, s>>>((const typename P::R *)state, rho, u, uy_off,
-                                                                    row0, rows, p)));
+    SMRT_MODE_SWITCH(mode, (macros_kernel<PREC, M><<<nb, 256, 0, s>>>((const typename P::R *)state, rho, u, row0, rows, p)));
     return cudaGetLastError();
 }
 
@@ -1094,9 +996,6 @@ KernelTable make_table()
     t.init_macros = &launch_init_macros<PREC>;
     t.macros = &launch_macros<PREC>;
     t.residual = &launch_residual<PREC>;
-    t.step_rows = &launch_step_rows<PREC>;
-    t.init_macros_rows = &launch_init_macros_rows<PREC>;
-    t.macros_rows = &launch_macros_rows<PREC>;
     t.elem_bytes = sizeof(typename Prec<PREC>::R);
     return t;
 }
