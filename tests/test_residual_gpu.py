@@ -81,3 +81,29 @@ def test_fp64_residual_with_interior_tiles_matches_the_oracle(layout):
     assert abs(r - r_ref) <= 1e-9 * r_ref, (r, r_ref)
     assert np.abs(np.array(sums) - np.array(sums_ref)).max() <= 1e-12 * nx * ny
     S.smrt_destroy(h)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("nx,ny", [(2, 2), (3, 2), (5, 3), (129, 3), (3, 129), (31, 5), (33, 70)])
+@pytest.mark.parametrize("bc", [W.CAVITY, W.ALL_PERIODIC, W.COUETTE])
+def test_residual_on_tiny_and_thin_lattices(nx, ny, bc):
+    """Strips narrower than a warp, segments shorter than the sweep, one-row interiors, wrapped
+    halos: FP64 against oracle.residual; FP32 against one real step."""
+    import oracle as O
+    tau, U = 0.7, (0.0 if bc == W.ALL_PERIODIC else 0.05)
+    rho, u = W.random_macros(nx, ny, 21, u_amp=0.02)
+    h = make(nx, ny, tau, U, bc)
+    S.smrt_init_macros(h, rho, u)
+    S.smrt_step(h, 3)
+    f = np.empty((9, ny, nx))
+    S.smrt_get_f(h, f)
+    r, sums = S.smrt_residual(h)
+    r_ref, sums_ref = O.residual(f, bc, tau, u_lid=U)
+    assert abs(r - r_ref) <= 1e-9 * r_ref, (r, r_ref)
+    assert np.abs(np.array(sums) - np.array(sums_ref)).max() <= 1e-12 * nx * ny
+    S.smrt_destroy(h)
+    h = make(nx, ny, tau, U, bc, prec="f32")
+    S.smrt_init_macros(h, rho, u)
+    S.smrt_step(h, 3)
+    _check_against_one_step(h)
+    S.smrt_destroy(h)
